@@ -1,0 +1,234 @@
+"""Pins of the CPU oracle against facts the paper and the mathematics fix.
+
+None of these retypes an oracle formula: each checks a closed form, an
+identity, an invariant, a textbook routine or a limit that a dropped term, a
+wrong sign or index or a transposed operand would break.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import stokes_inputs as si
+
+
+def _ellipse_geometry(orientation):
+    c = si.superellipse_curve(1.3, 0.6, 400, p=2)
+    if orientation == "cw":   # pore-like: traversal reversed, normal into the curve
+        c = si.Curve(c.nodes[::-1].copy(), -c.normals[::-1].copy(), c.weights[::-1].copy(),
+                     -c.curvature[::-1].copy(), c.centre, 0.0)
+    return si.assemble_geometry([], c)
+
+
+@pytest.mark.parametrize("orientation,sign", [("ccw", -1.0), ("cw", 1.0)])
+@pytest.mark.parametrize("e", [(1.0, 0.0), (0.0, 1.0), (0.6, -0.8)])
+def test_double_layer_of_constant_density(orientation, sign, e):
+    """Gauss-type identity for the Stokes double layer of Sec. 2.1 with a
+    constant density e: -e inside / 0 outside a curve whose normal points out
+    of it, and the mean -e/2 on the curve (principal value + diagonal entry).
+    Flipping the normal flips the sign."""
+    g = _ellipse_geometry(orientation)
+    e = np.asarray(e)
+    sig = np.tile(e, (g.n_nodes, 1))
+    inside = O.velocity(g, sig, np.array([[0.1, 0.05], [-0.9, 0.2], [0.0, -0.45]]))
+    outside = O.velocity(g, sig, np.array([[2.0, 1.0], [0.0, 1.5], [-1.6, 0.0]]))
+    assert np.abs(inside - sign * e).max() < 1e-12
+    assert np.abs(outside).max() < 1e-12
+    idx = np.arange(g.n_nodes)
+    B = O.operator_blocks(g, idx, idx, completion=False, outer_fix=False, jump=False)
+    on = np.einsum("ijab,jb->ia", B, sig)
+    assert np.abs(on - sign * 0.5 * e).max() < 1e-12
+    # the jump term makes the boundary value equal the limit from the
+    # fluid side (outside for "cw", inside for "ccw")
+    Bj = O.operator_blocks(g, idx, idx, completion=False, outer_fix=False, jump=True)
+    lim = np.einsum("ijab,jb->ia", Bj, sig)
+    assert np.abs(lim - (sign * e if orientation == "ccw" else 0 * e)).max() < 1e-12
+
+
+def test_diagonal_entry_is_the_kernel_limit():
+    """The j = i entry equals the limit of the kernel as the source slides
+    along the curve onto the target (ellipse, both orientations)."""
+    for orientation in ("ccw", "cw"):
+        g = _ellipse_geometry(orientation)
+        S = O.self_blocks(g)
+        for i in (0, 37, 150):
+            # exact nearby point on the ellipse (parametric), its normal from the same curve
+            th = np.arctan2(g.nodes[i, 1] / 0.6, g.nodes[i, 0] / 1.3)
+            for eps in (1e-3,):
+                y = np.array([[1.3 * np.cos(th + eps), 0.6 * np.sin(th + eps)]])
+                t = np.array([-1.3 * np.sin(th + eps), 0.6 * np.cos(th + eps)])
+                n = np.array([t[1], -t[0]]) / np.linalg.norm(t)
+                if orientation == "cw":
+                    n = -n
+                K = O.dlp_kernel(g.nodes[i:i + 1], y, n[None])[0, 0]
+                assert np.abs(K * g.weights[i] - S[i]).max() < 5e-3 * np.abs(S[i]).max() + 1e-12
+
+
+def test_self_term_is_needed():
+    """Dropping the diagonal term breaks the on-curve identity for a
+    tangential density (a planted mistake the identity test must catch)."""
+    g = _ellipse_geometry("ccw")
+    t = np.stack([-g.normals[:, 1], g.normals[:, 0]], 1)
+    idx = np.arange(g.n_nodes)
+    B = O.operator_blocks(g, idx, idx, completion=False, outer_fix=False, jump=False)
+    sig = np.tile([1.0, 0.0], (g.n_nodes, 1))
+    B_noself = B.copy()
+    B_noself[idx, idx] = 0.0
+    bad = np.einsum("ijab,jb->ia", B_noself, sig)
+    assert np.abs(bad + 0.5 * sig).max() > 1e-3
+
+
+def test_null_space_rank_without_completion(small_geom):
+    """Sec. 2.1: the double layer has a rank-3 null space per pore (rigid
+    motions); the interior problem adds a rank-1 defect on the wall. The
+    completion of each pore and the wall term remove all of them."""
+    g = small_geom
+    sv0 = np.linalg.svd(O.assemble(g, completion=False, outer_fix=False), compute_uv=False)
+    tiny = (sv0 < 1e-7 * sv0[0]).sum()
+    assert tiny == 3 * g.n_pores + 1
+    assert sv0[-(3 * g.n_pores + 2)] > 1e-3 * sv0[0]
+    sv = np.linalg.svd(O.assemble(g), compute_uv=False)
+    assert sv[-1] > 1e-3
+
+
+def test_smallest_singular_value_stable_under_refinement():
+    """A second-kind system: the smallest singular value does not decay as
+    the mesh is refined."""
+    smins = []
+    for npp, no in ((16, 128), (32, 256), (64, 512)):
+        g = si.config1_geometry(1, n_outer=no, n_pores=3, n_per_pore=npp)
+        smins.append(np.linalg.svd(O.assemble(g), compute_uv=False)[-1])
+    assert smins[-1] > 0.5 * smins[0]
+
+
+@pytest.fixture(scope="module")
+def fine_geom():
+    return si.config1_geometry(2, n_outer=512, n_pores=4, n_per_pore=64)
+
+
+@pytest.mark.parametrize("case", ["translation", "rotation", "shear"])
+def test_exact_rigid_and_shear_flows(fine_geom, case):
+    """Translation, rotation and the shear flow of Sec. 4.1 on every boundary
+    are Stokes flows: the computed velocity must reproduce them in the
+    interior, and (as Sec. 4.1 notes for shear) the pore densities vanish."""
+    g = fine_geom
+    f = {"translation": si.translation_bc, "rotation": si.rotation_bc, "shear": si.shear_bc}[case](g)
+    s = O.solve_dense(g, f)
+    T = si.interior_targets(g, 300, min_dist=0.3, seed=4)
+    u = O.velocity(g, s, T)
+    exact = {"translation": si.translation_bc, "rotation": si.rotation_bc, "shear": si.shear_bc}
+    tmp = si.Geometry(T, T, np.ones(len(T)), np.ones(len(T)), np.array([0, len(T)]), 0,
+                      np.zeros((1, 2)), np.zeros(1))
+    ue = exact[case](tmp)
+    assert np.abs(u - ue).max() < 1e-9 * max(1.0, np.abs(ue).max())
+    pores = 2 * int(g.offsets[g.outer_comp])
+    assert np.abs(s[:pores]).max() < 1e-7 * np.abs(s[pores:]).max()
+    lam, xi, s0 = O.moments(g, s)
+    assert abs(s0) < 1e-12
+
+
+def test_stokeslet_rotlet_exact_and_spectral_convergence():
+    """Eq. 13 data (Stokeslets and rotlets inside the pores and outside the
+    wall) has the closed-form velocity of Eq. 13; the error decays
+    geometrically under refinement (trapezoid rule on analytic curves)."""
+    errs = []
+    for npp, no in ((16, 128), (32, 256), (64, 512)):
+        g = si.config1_geometry(2, n_outer=no, n_pores=4, n_per_pore=npp)
+        c, lam, mu = si.stokeslet_rotlet_params(g, 0)
+        s = O.solve_dense(g, si.stokeslet_rotlet_velocity(g.nodes, c, lam, mu))
+        T = si.interior_targets(g, 200, min_dist=0.3, seed=5)
+        ue = si.stokeslet_rotlet_velocity(T, c, lam, mu)
+        errs.append(np.abs(O.velocity(g, s, T) - ue).max() / np.abs(ue).max())
+        if npp == 64:
+            pores = 2 * int(g.offsets[g.outer_comp])
+            assert np.abs(s[:pores]).max() > 1e-2     # non-zero pore densities
+    assert errs[-1] < 1e-9
+    assert errs[1] < 1e-2 * errs[0] and errs[2] < 1e-2 * errs[1]
+
+
+def test_matrix_free_rows_match_dense(small_geom):
+    g = small_geom
+    A = O.assemble(g)
+    sig = si.random_density(g, 1)
+    assert np.abs(O.matvec(g, sig) - A @ sig.reshape(-1)).max() < 1e-12 * np.abs(A).max() * g.n_nodes
+    rows = np.array([0, 5, 100, g.n_nodes - 1])
+    got = O.apply_rows(g, sig, rows).reshape(-1)
+    idx = np.stack([2 * rows, 2 * rows + 1], 1).reshape(-1)
+    assert np.allclose(got, (A @ sig.reshape(-1))[idx], rtol=0, atol=1e-12)
+
+
+def test_moments_match_completion_columns(small_geom):
+    """A sigma - A_nocompletion sigma equals the Stokeslet/rotlet field of the
+    moments (checks the moment definitions against the assembled columns)."""
+    g = small_geom
+    sig = si.random_density(g, 2)
+    d = (O.assemble(g) - O.assemble(g, completion=False)) @ sig.reshape(-1)
+    lam, xi, _ = O.moments(g, sig)
+    u = np.zeros((g.n_nodes, 2))
+    for k in range(g.n_pores):
+        u += np.einsum("tab,b->ta", O.stokeslet(g.nodes, g.centres[k]), lam[k])
+        u += O.rotlet(g.nodes, g.centres[k]) * xi[k]
+    assert np.abs(d - u.reshape(-1)).max() < 1e-12
+
+
+def test_gmres_matches_dense_lu(small_geom):
+    """Restarted GMRES (Sec. 4, Saad-Schultz) against LAPACK LU, with and
+    without the block-diagonal preconditioner, right and left."""
+    g = small_geom
+    f = si.pipe_bc(g)
+    sd = O.solve_dense(g, f)
+    for pc in ("bd", None):
+        r = O.solve_gmres(g, f, tol=1e-12, restart=20, precond=pc, side="right")
+        assert r["relres"] <= 1e-12
+        assert np.linalg.norm(r["x"] - sd) < 1e-10 * np.linalg.norm(sd)
+    r = O.solve_gmres(g, f, tol=1e-12, restart=20, precond="bd", side="left")
+    assert r["pc_relres"] <= 1e-12 and r["relres"] < 1e-10
+
+
+def test_block_diagonal_is_exact_inverse_of_blocks(small_geom):
+    """Each preconditioner block is the restriction of A to one component
+    (Sec. 4.1 footnote), applied exactly."""
+    g = small_geom
+    A = O.assemble(g)
+    bd = O.BlockDiagonal(g)
+    v = np.random.default_rng(0).standard_normal(2 * g.n_nodes)
+    z = bd.apply(v)
+    for k in range(g.n_comp):
+        a, b = 2 * int(g.offsets[k]), 2 * int(g.offsets[k + 1])
+        assert np.allclose(A[a:b, a:b] @ z[a:b], v[a:b], rtol=0, atol=1e-11)
+        assert np.array_equal(bd.blocks[k], A[a:b, a:b])
+
+
+def test_bd_gmres_fewer_iterations_than_none(cfg1_geom):
+    """Sec. 4.1: block-diagonal preconditioning cuts the iteration count."""
+    f = si.pipe_bc(cfg1_geom)
+    r_bd = O.solve_gmres(cfg1_geom, f, tol=1e-8, restart=50, precond="bd")
+    r_no = O.solve_gmres(cfg1_geom, f, tol=1e-8, restart=50, precond=None)
+    assert r_bd["relres"] <= 1e-8 and r_no["relres"] <= 1e-8
+    assert r_bd["iters"] < 0.5 * r_no["iters"]
+
+
+def test_pipe_flow_no_net_flux_around_a_pore(cfg1_geom):
+    """Incompressibility and no slip (Eq. 1-2): the flux of u through any
+    closed curve in the fluid that encloses one pore is zero; the flux
+    through a vertical cut equals the flux leaving the wall beyond it."""
+    g = cfg1_geom
+    f = si.pipe_bc(g)
+    s = O.solve_gmres(g, f, tol=1e-12, restart=50)["x"]
+    pc, pr = g.centres[: g.n_pores], g.radii[: g.n_pores]
+    for k in range(g.n_pores):
+        R = pr[k] + 0.025
+        others = np.delete(np.arange(g.n_pores), k)
+        if (np.linalg.norm(pc[others] - pc[k], axis=1) - pr[others] < R + 0.02).any():
+            continue
+        th = 2 * np.pi * np.arange(256) / 256
+        pts = pc[k] + R * np.stack([np.cos(th), np.sin(th)], 1)
+        u = O.velocity(g, s, pts)
+        flux = (u * np.stack([np.cos(th), np.sin(th)], 1)).sum() * (2 * np.pi * R / 256)
+        scale = (np.abs(u).sum(1)).mean() * 2 * np.pi * R
+        assert abs(flux) < 1e-9 * max(scale, 1e-3)
+    # the velocity reproduces the data on the boundary from the fluid side
+    # when evaluated just inside the wall near the intake centre
+    x0 = np.array([[-3.9, 0.0]])
+    assert abs(O.velocity(g, s, x0)[0, 0] - 1.0) < 0.05
