@@ -1,0 +1,167 @@
+/*
+ * stokes.h -- C ABI of the GB300 double-layer Stokes solver (libstokes.so).
+ *
+ * The library solves the boundary-integral system of a 2D Stokes flow in a
+ * porous pipe (Coulier, Quaife & Darve, "An efficient preconditioner for the
+ * fast simulation of a 2D Stokes flow in porous media"): the domain is the
+ * region inside an outer wall Gamma_0 and outside M pores (Sec. 2, Eq. 1),
+ * the velocity is prescribed on the whole boundary (Eq. 2 for the pipe
+ * flow), and the velocity is represented by the double-layer potential of
+ * Sec. 2.1, discretised by collocation at trapezoid-rule nodes (Sec. 2.2,
+ * Eq. 5-6). The discrete operator applied to a density sigma is, at node i,
+ *
+ *   (A sigma)_i = -sigma_i / 2
+ *              + sum_{j != i} (w_j / pi) (r.n_j)(r.sigma_j) r / rho^4      r = x_i - x_j
+ *              + w_i (-kappa_i / (2 pi)) t_i (t_i . sigma_i)            t = (-n_y, n_x)
+ *              + sum_{pores k} S(x_i, c_k) lambda_k + R(x_i, c_k) xi_k
+ *              + [i on Gamma_0] n_i sum_{j on Gamma_0} w_j n_j . sigma_j
+ *
+ * with S(x, c) = (1/4pi)(-log rho I + r r^T / rho^2), R(x, c) = (1/4pi) r^perp / rho^2,
+ * r = x - c, (a, b)^perp = (b, -a), lambda_k = sum_{j in k} w_j sigma_j and
+ * xi_k = sum_{j in k} w_j (x_j - c_k)^perp . sigma_j. The paper states the
+ * kernel and that its rank-3-per-component null space "can be removed"
+ * (Sec. 2.1); the diagonal entry (the kernel's limit on a smooth curve), the
+ * -1/2 jump, the Stokeslet/rotlet completion and the wall term are the
+ * standard completed double-layer formulation chosen to remove it.
+ *
+ * Conventions for every call:
+ *  - Nodes are grouped by component, pores and wall in any order given by
+ *    `offsets`; vectors on nodes are interleaved (x, y) pairs, so a density or
+ *    a right-hand side is 2N doubles [sx_0, sy_0, sx_1, sy_1, ...].
+ *  - Normals are unit vectors pointing OUT OF THE FLUID (out of Gamma_0, into
+ *    each pore); kappa is the signed curvature with kappa > 0 on a convex
+ *    wall and kappa = -1/R on a pore of radius R.
+ *  - Array arguments may be HOST or DEVICE pointers (the library checks with
+ *    cudaPointerGetAttributes and copies host data through its own device
+ *    buffers); the caller keeps ownership of every array it passes. A handle
+ *    owns its device copies, preconditioner factors and workspaces.
+ *  - All GPU work of a handle runs on the CUDA stream given at creation.
+ *    Calls that return scalars (iteration counts, residuals) or write HOST
+ *    outputs synchronise that stream; others are asynchronous.
+ *  - Every function returns a status (STOKES_OK = 0 or a negative code);
+ *    stokes_last_error() returns a thread-local message for the last failure.
+ *    No C++ exception crosses the ABI. A handle is not thread-safe.
+ */
+#ifndef STOKES_H
+#define STOKES_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum stokes_status {
+  STOKES_OK = 0,
+  STOKES_EINVAL = -1,     /* bad argument (sizes, offsets, null pointers, values) */
+  STOKES_ENOMEM = -2,     /* device allocation failed */
+  STOKES_ECUDA = -3,      /* a CUDA call failed; see stokes_last_error() */
+  STOKES_ENOTCONV = -4,   /* GMRES hit max_iter; outputs hold the last iterate */
+  STOKES_EBREAKDOWN = -5, /* non-finite residual (NaN/Inf) */
+  STOKES_ESTATE = -6      /* call order: e.g. precond apply before setup */
+};
+
+/* Arithmetic of the discrete operator.
+ * STOKES_FP64: native double precision everywhere.
+ * STOKES_FP32: single precision pair sums (node coordinates taken relative to
+ *   their component's centre), double-precision moments and outputs.
+ * STOKES_DF64: double-float pair sums (unevaluated sums of two floats with
+ *   error-free transformations) giving FP64-class accuracy on the FP32 pipes.
+ * STOKES_MIXED_IR (solve only): FP32 inner GMRES inside FP64 iterative
+ *   refinement; the outer residual uses the DF64 operator. */
+enum stokes_precision {
+  STOKES_FP64 = 0,
+  STOKES_FP32 = 1,
+  STOKES_DF64 = 2,
+  STOKES_MIXED_IR = 3
+};
+
+enum stokes_pc_kind { STOKES_PC_NONE = 0, STOKES_PC_BLOCKDIAG = 1 };
+enum stokes_pc_side { STOKES_PC_RIGHT = 0, STOKES_PC_LEFT = 1 };
+
+typedef struct stokes_geom stokes_geom;
+
+/* Build a handle from the discrete boundary (Sec. 2.2: nodes are the
+ * collocation points, weights the arclength quadrature weights).
+ *   nodes     [2N]   node positions, interleaved (x, y)
+ *   normals   [2N]   unit normals, out of the fluid
+ *   weights   [N]    quadrature weights, > 0
+ *   curvature [N]    signed curvature (see conventions)
+ *   offsets   [n_comp+1] HOST int64, offsets[0] = 0, strictly increasing by
+ *             at least 8 nodes; component c owns nodes [offsets[c], offsets[c+1])
+ *   n_comp    number of components (>= 1); outer_comp in [0, n_comp) is Gamma_0
+ *   centres   [2 n_comp] HOST, the completion centre c_k of each pore (the
+ *             wall's entry is ignored), or NULL for the quadrature centroid
+ *             sum w x / sum w of each component
+ *   stream    cudaStream_t (NULL = legacy default stream)
+ *   out       receives the handle; unchanged on error
+ * Errors: STOKES_EINVAL (sizes, offsets, non-finite or non-positive weights,
+ * normals off unit length by > 1e-6), STOKES_ENOMEM, STOKES_ECUDA. */
+int stokes_geometry_create(const double* nodes, const double* normals, const double* weights,
+                           const double* curvature, const int64_t* offsets, int n_comp,
+                           int outer_comp, const double* centres, void* stream,
+                           stokes_geom** out);
+
+/* Free a handle and everything it owns (NULL is a no-op). */
+int stokes_geometry_destroy(stokes_geom* g);
+
+/* Number of nodes N of a handle (unknowns are 2N); -1 for NULL. */
+int64_t stokes_geometry_num_nodes(const stokes_geom* g);
+
+/* y = A sigma (the operator above, Eq. 6 for the double-layer system).
+ *   sigma [2N] in, y [2N] out (host or device; may not alias)
+ *   precision: STOKES_FP64, STOKES_FP32 or STOKES_DF64.
+ * Errors: STOKES_EINVAL, STOKES_ECUDA. */
+int stokes_matvec(stokes_geom* g, const double* sigma, double* y, int precision);
+
+/* Build the preconditioner (Sec. 4.1 and its footnote): block diagonal with
+ * one block per component, the restriction of A to that component
+ * (including its own completion or wall term), assembled on the GPU,
+ * LU-factorised with partial pivoting in FP64 and inverted exactly.
+ *   pc_kind: STOKES_PC_NONE (drops any existing factors) or STOKES_PC_BLOCKDIAG.
+ * Errors: STOKES_EINVAL, STOKES_ENOMEM, STOKES_ECUDA; a singular block
+ * (zero pivot) gives STOKES_EBREAKDOWN. */
+int stokes_precond_setup(stokes_geom* g, int pc_kind);
+
+/* z = P^-1 v with the block-diagonal preconditioner (for tests and
+ * external Krylov codes). v, z [2N]. STOKES_ESTATE if not set up. */
+int stokes_precond_apply(stokes_geom* g, const double* v, double* z);
+
+/* Solve A sigma = f by restarted GMRES (Sec. 4: GMRES of Saad and Schultz,
+ * relative-residual tolerance) with the preconditioner of the last
+ * stokes_precond_setup call (none if never set up).
+ *   f       [2N] right-hand side (the boundary data at the nodes)
+ *   tol     relative residual tolerance (> 0)
+ *   restart Krylov dimension per cycle, 1..200
+ *   max_iter total inner iterations (>= 1)
+ *   precision STOKES_FP64, STOKES_DF64 (operator arithmetic; Arnoldi, Givens
+ *             and the least-squares update always FP64) or STOKES_MIXED_IR
+ *   pc_side STOKES_PC_RIGHT (default; stops on the true residual
+ *           |f - A sigma| / |f|) or STOKES_PC_LEFT (Sec. 4.1; stops on the
+ *           preconditioned residual |P^-1 (f - A sigma)| / |P^-1 f|)
+ *   sigma   [2N] in: initial guess; out: solution
+ *   iters_out, true_relres_out, pc_relres_out: HOST scalars (may be NULL)
+ * Returns STOKES_OK on convergence, STOKES_ENOTCONV at max_iter (sigma holds
+ * the last iterate), STOKES_EBREAKDOWN on a non-finite residual. */
+int stokes_gmres_solve(stokes_geom* g, const double* f, double tol, int restart, int max_iter,
+                       int precision, int pc_side, double* sigma, int* iters_out,
+                       double* true_relres_out, double* pc_relres_out);
+
+/* Velocity at points inside the fluid (Sec. 2.2, Eq. 7 with the
+ * double-layer kernel): u(x) = sum_j (w_j / pi)(r.n_j)(r.sigma_j) r / rho^4
+ * + sum_k S(x, c_k) lambda_k + R(x, c_k) xi_k, r = x - x_j (no jump, no
+ * diagonal term, no wall term). Accurate when the target is farther than
+ * about the local node spacing from the boundary (Sec. 2.2 footnote).
+ *   sigma [2N]; targets [2T]; u [2T]; precision FP64, FP32 or DF64.
+ * A target on a node gives a non-finite value for that target. */
+int stokes_eval_velocity(stokes_geom* g, const double* sigma, const double* targets,
+                         int64_t n_targets, double* u, int precision);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* stokes_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STOKES_H */

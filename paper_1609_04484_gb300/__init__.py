@@ -1,0 +1,185 @@
+"""GB300 double-layer Stokes solver: Python binding of libstokes.so.
+
+The functions below have the names of the C ABI in include/stokes.h and do
+argument marshalling only: every step of the computation runs in the CUDA
+library. Arrays may be numpy arrays (host memory) or torch tensors (host or
+CUDA); they must be C-contiguous float64 (offsets/centres: host). Importing
+this package raises if the compiled library is missing: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import pathlib
+
+import numpy as np
+
+__all__ = [
+    "STOKES_OK", "STOKES_EINVAL", "STOKES_ENOMEM", "STOKES_ECUDA", "STOKES_ENOTCONV",
+    "STOKES_EBREAKDOWN", "STOKES_ESTATE", "STOKES_FP64", "STOKES_FP32", "STOKES_DF64",
+    "STOKES_MIXED_IR", "STOKES_PC_NONE", "STOKES_PC_BLOCKDIAG", "STOKES_PC_RIGHT", "STOKES_PC_LEFT",
+    "StokesError", "lib", "library_path", "stokes_geometry_create", "stokes_geometry_destroy",
+    "stokes_geometry_num_nodes", "stokes_matvec", "stokes_precond_setup", "stokes_precond_apply",
+    "stokes_gmres_solve", "stokes_eval_velocity", "stokes_last_error", "Geometry",
+]
+
+STOKES_OK, STOKES_EINVAL, STOKES_ENOMEM, STOKES_ECUDA = 0, -1, -2, -3
+STOKES_ENOTCONV, STOKES_EBREAKDOWN, STOKES_ESTATE = -4, -5, -6
+STOKES_FP64, STOKES_FP32, STOKES_DF64, STOKES_MIXED_IR = 0, 1, 2, 3
+STOKES_PC_NONE, STOKES_PC_BLOCKDIAG = 0, 1
+STOKES_PC_RIGHT, STOKES_PC_LEFT = 0, 1
+
+_PKG = pathlib.Path(__file__).resolve().parent
+library_path = _PKG / "lib" / "libstokes.so"
+
+
+class StokesError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+def _load():
+    if not library_path.exists():
+        raise ImportError(f"libstokes.so not built ({library_path}); run __graft_entry__.build()")
+    L = ctypes.CDLL(str(library_path))
+    P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "stokes_geometry_create": (I, [P, P, P, P, P, I, I, P, P, ctypes.POINTER(P)]),
+        "stokes_geometry_destroy": (I, [P]),
+        "stokes_geometry_num_nodes": (I64, [P]),
+        "stokes_matvec": (I, [P, P, P, I]),
+        "stokes_precond_setup": (I, [P, I]),
+        "stokes_precond_apply": (I, [P, P, P]),
+        "stokes_gmres_solve": (I, [P, P, D, I, I, I, I, P, ctypes.POINTER(I), ctypes.POINTER(D),
+                                   ctypes.POINTER(D)]),
+        "stokes_eval_velocity": (I, [P, P, P, I64, P, I]),
+        "stokes_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    return L
+
+
+lib = _load()
+
+
+def stokes_last_error() -> str:
+    return lib.stokes_last_error().decode()
+
+
+def _check(code, allow=()):
+    if code != STOKES_OK and code not in allow:
+        raise StokesError(code, stokes_last_error())
+    return code
+
+
+def _ptr(a, dtype=np.float64, count=None):
+    """Address of a C-contiguous numpy array or torch tensor (host or CUDA)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):  # torch.Tensor
+        import torch
+        want = {np.float64: torch.float64, np.int64: torch.int64}[dtype]
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"tensor must be contiguous {want}")
+        if count is not None and a.numel() != count:
+            raise ValueError(f"expected {count} elements, got {a.numel()}")
+        return ctypes.c_void_p(a.data_ptr())
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"array must be a C-contiguous {np.dtype(dtype).name} numpy array or tensor")
+    if count is not None and a.size != count:
+        raise ValueError(f"expected {count} elements, got {a.size}")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def stokes_geometry_create(nodes, normals, weights, curvature, offsets, n_comp, outer_comp,
+                           centres=None, stream=None):
+    """Returns an opaque handle (int). See include/stokes.h."""
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    N = int(off[-1])
+    cen = None if centres is None else np.ascontiguousarray(centres, dtype=np.float64)
+    h = ctypes.c_void_p()
+    st = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(lib.stokes_geometry_create(_ptr(nodes, count=2 * N), _ptr(normals, count=2 * N),
+                                      _ptr(weights, count=N), _ptr(curvature, count=N),
+                                      _ptr(off, np.int64), int(n_comp), int(outer_comp),
+                                      _ptr(cen), st, ctypes.byref(h)))
+    return h.value
+
+
+def stokes_geometry_destroy(handle):
+    _check(lib.stokes_geometry_destroy(ctypes.c_void_p(handle)))
+
+
+def stokes_geometry_num_nodes(handle) -> int:
+    return int(lib.stokes_geometry_num_nodes(ctypes.c_void_p(handle)))
+
+
+def stokes_matvec(handle, sigma, y, precision=STOKES_FP64):
+    n2 = 2 * stokes_geometry_num_nodes(handle)
+    _check(lib.stokes_matvec(ctypes.c_void_p(handle), _ptr(sigma, count=n2), _ptr(y, count=n2), int(precision)))
+
+
+def stokes_precond_setup(handle, pc_kind=STOKES_PC_BLOCKDIAG):
+    _check(lib.stokes_precond_setup(ctypes.c_void_p(handle), int(pc_kind)))
+
+
+def stokes_precond_apply(handle, v, z):
+    n2 = 2 * stokes_geometry_num_nodes(handle)
+    _check(lib.stokes_precond_apply(ctypes.c_void_p(handle), _ptr(v, count=n2), _ptr(z, count=n2)))
+
+
+def stokes_gmres_solve(handle, f, sigma, tol=1e-8, restart=50, max_iter=2000,
+                       precision=STOKES_FP64, pc_side=STOKES_PC_RIGHT):
+    """Solves in place into `sigma` (its content is the initial guess).
+    Returns (status, iters, true_relres, pc_relres); status is STOKES_OK or
+    STOKES_ENOTCONV, other failures raise."""
+    n2 = 2 * stokes_geometry_num_nodes(handle)
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    pr = ctypes.c_double(0.0)
+    code = lib.stokes_gmres_solve(ctypes.c_void_p(handle), _ptr(f, count=n2), float(tol), int(restart),
+                                  int(max_iter), int(precision), int(pc_side), _ptr(sigma, count=n2),
+                                  ctypes.byref(it), ctypes.byref(rr), ctypes.byref(pr))
+    _check(code, allow=(STOKES_ENOTCONV,))
+    return code, it.value, rr.value, pr.value
+
+
+def stokes_eval_velocity(handle, sigma, targets, u, precision=STOKES_FP64):
+    n2 = 2 * stokes_geometry_num_nodes(handle)
+    T = (targets.numel() if hasattr(targets, "numel") else targets.size) // 2
+    _check(lib.stokes_eval_velocity(ctypes.c_void_p(handle), _ptr(sigma, count=n2), _ptr(targets, count=2 * T),
+                                    ctypes.c_int64(T), _ptr(u, count=2 * T), int(precision)))
+
+
+class Geometry:
+    """Owning wrapper of a handle built from a stokes_inputs.Geometry-like
+    object (nodes, normals, weights, curvature, offsets, outer_comp, centres)."""
+
+    def __init__(self, geom, stream=None, centres=True):
+        arr = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+        self.N = int(geom.offsets[-1])
+        self.handle = stokes_geometry_create(
+            arr(geom.nodes).reshape(-1), arr(geom.normals).reshape(-1), arr(geom.weights),
+            arr(geom.curvature), geom.offsets, len(geom.offsets) - 1, geom.outer_comp,
+            arr(geom.centres).reshape(-1) if centres else None, stream)
+
+    def close(self):
+        if self.handle:
+            stokes_geometry_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,200 @@
+// extern "C" entry points of libstokes (declared in include/stokes.h).
+// Each call validates its arguments, stages host arrays through handle-owned
+// device buffers, runs the device path and maps failures to status codes.
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "internal.cuh"
+
+struct stokes_geom {
+  stokes::Geom* g;
+};
+
+namespace stokes {
+Geom* geometry_create(const double*, const double*, const double*, const double*, const int64_t*, int, int,
+                      const double*, void*);
+bool is_device_pointer(const void* p);
+}  // namespace stokes
+
+namespace {
+
+thread_local std::string g_last_error;
+
+template <class F>
+int guarded(F&& fn) {
+  try {
+    fn();
+    g_last_error.clear();
+    return STOKES_OK;
+  } catch (const stokes::Error& e) {
+    g_last_error = e.what();
+    return e.code;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return STOKES_ECUDA;
+  } catch (...) {
+    g_last_error = "unknown error";
+    return STOKES_ECUDA;
+  }
+}
+
+using stokes::DevBuf;
+using stokes::Geom;
+
+// A device view of a caller array: the caller's pointer if it is device
+// memory, else a handle-owned staging buffer filled from the host.
+const double* input_view(Geom& g, const double* p, size_t count, DevBuf<double2>& stage) {
+  if (stokes::is_device_pointer(p)) return p;
+  stage.alloc((count + 1) / 2);
+  STOKES_CUDA(cudaMemcpyAsync(stage.get(), p, count * sizeof(double), cudaMemcpyHostToDevice, g.stream));
+  return (const double*)stage.get();
+}
+
+double* output_view(Geom& g, double* p, size_t count, DevBuf<double2>& stage, bool& staged) {
+  staged = !stokes::is_device_pointer(p);
+  if (!staged) return p;
+  stage.alloc((count + 1) / 2);
+  return (double*)stage.get();
+}
+
+void finish_output(Geom& g, double* user, const double* dev, size_t count, bool staged) {
+  if (staged) {
+    STOKES_CUDA(cudaMemcpyAsync(user, dev, count * sizeof(double), cudaMemcpyDeviceToHost, g.stream));
+    STOKES_CUDA(cudaStreamSynchronize(g.stream));
+  }
+}
+
+Geom& handle(stokes_geom* h) {
+  stokes::require(h && h->g, "null handle");
+  return *h->g;
+}
+
+}  // namespace
+
+extern "C" {
+
+int stokes_geometry_create(const double* nodes, const double* normals, const double* weights,
+                           const double* curvature, const int64_t* offsets, int n_comp, int outer_comp,
+                           const double* centres, void* stream, stokes_geom** out) {
+  return guarded([&] {
+    stokes::require(out != nullptr, "out is null");
+    Geom* g = stokes::geometry_create(nodes, normals, weights, curvature, offsets, n_comp, outer_comp, centres,
+                                      stream);
+    *out = new stokes_geom{g};
+  });
+}
+
+int stokes_geometry_destroy(stokes_geom* h) {
+  return guarded([&] {
+    if (!h) return;
+    if (h->g) {
+      cudaStreamSynchronize(h->g->stream);
+      delete h->g;
+    }
+    delete h;
+  });
+}
+
+int64_t stokes_geometry_num_nodes(const stokes_geom* h) { return (h && h->g) ? h->g->N : -1; }
+
+int stokes_matvec(stokes_geom* h, const double* sigma, double* y, int precision) {
+  return guarded([&] {
+    Geom& g = handle(h);
+    stokes::require(sigma && y, "null array argument");
+    stokes::require(sigma != y, "sigma and y may not alias");
+    stokes::require(precision == STOKES_FP64 || precision == STOKES_FP32 || precision == STOKES_DF64,
+                    "precision must be FP64, FP32 or DF64");
+    const size_t n = 2 * g.N;
+    const double* s = input_view(g, sigma, n, g.stage_in);
+    bool staged;
+    double* yo = output_view(g, y, n, g.stage_out, staged);
+    stokes::apply_operator(g, s, yo, precision, nullptr);
+    STOKES_LAUNCHED();
+    finish_output(g, y, yo, n, staged);
+  });
+}
+
+int stokes_precond_setup(stokes_geom* h, int pc_kind) {
+  return guarded([&] {
+    Geom& g = handle(h);
+    stokes::require(pc_kind == STOKES_PC_NONE || pc_kind == STOKES_PC_BLOCKDIAG, "unknown pc_kind");
+    if (pc_kind == STOKES_PC_NONE) {
+      g.bd.ready = false;
+      g.bd.lu.release();
+      g.bd.inv.release();
+      return;
+    }
+    stokes::bd_setup(g);
+  });
+}
+
+int stokes_precond_apply(stokes_geom* h, const double* v, double* z) {
+  return guarded([&] {
+    Geom& g = handle(h);
+    stokes::require(v && z && v != z, "bad array arguments");
+    stokes::require(g.bd.ready, "preconditioner not set up", STOKES_ESTATE);
+    const size_t n = 2 * g.N;
+    const double* vi = input_view(g, v, n, g.stage_in);
+    bool staged;
+    double* zo = output_view(g, z, n, g.stage_out, staged);
+    stokes::bd_apply(g, vi, zo, nullptr);
+    STOKES_LAUNCHED();
+    finish_output(g, z, zo, n, staged);
+  });
+}
+
+int stokes_gmres_solve(stokes_geom* h, const double* f, double tol, int restart, int max_iter, int precision,
+                       int pc_side, double* sigma, int* iters_out, double* true_relres_out,
+                       double* pc_relres_out) {
+  int solve_status = STOKES_OK;
+  const int rc = guarded([&] {
+    Geom& g = handle(h);
+    stokes::require(f && sigma && f != sigma, "bad array arguments");
+    stokes::require(precision == STOKES_FP64 || precision == STOKES_DF64 || precision == STOKES_MIXED_IR,
+                    "precision must be FP64, DF64 or MIXED_IR");
+    stokes::require(pc_side == STOKES_PC_RIGHT || pc_side == STOKES_PC_LEFT, "bad pc_side");
+    const size_t n = 2 * g.N;
+    const double* fi = input_view(g, f, n, g.stage_in);
+    // sigma is read (initial guess) and written: work in a device copy when on the host
+    bool staged = !stokes::is_device_pointer(sigma);
+    double* x = sigma;
+    if (staged) {
+      g.stage_out.alloc(g.N);
+      x = (double*)g.stage_out.get();
+      STOKES_CUDA(cudaMemcpyAsync(x, sigma, n * sizeof(double), cudaMemcpyHostToDevice, g.stream));
+    }
+    stokes::SolveResult r = stokes::gmres_solve(g, fi, x, tol, restart, max_iter, precision, pc_side);
+    finish_output(g, sigma, x, n, staged);
+    if (iters_out) *iters_out = r.iters;
+    if (true_relres_out) *true_relres_out = r.relres;
+    if (pc_relres_out) *pc_relres_out = r.pc_relres;
+    solve_status = r.status;
+  });
+  if (rc != STOKES_OK) return rc;
+  if (solve_status != STOKES_OK) {
+    g_last_error = solve_status == STOKES_ENOTCONV ? "GMRES reached max_iter" : "GMRES: non-finite residual";
+  }
+  return solve_status;
+}
+
+int stokes_eval_velocity(stokes_geom* h, const double* sigma, const double* targets, int64_t n_targets, double* u,
+                         int precision) {
+  return guarded([&] {
+    Geom& g = handle(h);
+    stokes::require(sigma && targets && u, "null array argument");
+    stokes::require(n_targets >= 0, "n_targets must be >= 0");
+    stokes::require(precision == STOKES_FP64, "precision must be FP64 for velocity evaluation");
+    if (n_targets == 0) return;
+    const double* s = input_view(g, sigma, 2 * g.N, g.stage_in);
+    const double* t = input_view(g, targets, 2 * n_targets, g.stage_tgt);
+    bool staged;
+    double* uo = output_view(g, u, 2 * n_targets, g.stage_out, staged);
+    stokes::dlp_apply_f64(g, (const double2*)s, (double2*)uo, false, (const double2*)t, n_targets, nullptr);
+    finish_output(g, u, uo, 2 * n_targets, staged);
+  });
+}
+
+const char* stokes_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

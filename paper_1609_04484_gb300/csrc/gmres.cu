@@ -1,0 +1,390 @@
+// Restarted GMRES on the device (Sec. 4: GMRES of Saad and Schultz with a
+// relative-residual tolerance; Sec. 4.1: preconditioning).
+//
+// Each Arnoldi step: z = P^-1 v_j (right) or t = A v_j (left), w = A z or
+// P^-1 t, classical Gram-Schmidt applied twice (CGS2: dot products as
+// warp-level reductions over chunks of the vector, deterministic two-level
+// sums), normalisation, then one thread applies the Givens rotations,
+// updates the least-squares residual and raises a device flag when it drops
+// below tol. Every kernel of a cycle reads that flag and returns at once
+// once it is set, so the host only synchronises at the end of each cycle to
+// read the column count and the true residual.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace stokes {
+
+namespace {
+
+constexpr int kChunk = 2048;  // vector elements per CTA in the reductions
+constexpr int kMaxRestart = 200;
+
+// partial[b * ldp + k] = sum_{i in chunk b} V[k][i] w[i], k < ncols
+__global__ void __launch_bounds__(256)
+k_dot_partial(const double* __restrict__ V, int64_t ldv, int ncols, const double* __restrict__ w, int64_t n,
+              double* __restrict__ partial, int ldp, const int* __restrict__ done) {
+  if (done && *done) return;
+  __shared__ double sw[kChunk];
+  const int64_t i0 = blockIdx.x * (int64_t)kChunk;
+  const int cn = (int)imin64(kChunk, n - i0);
+  for (int e = threadIdx.x; e < cn; e += blockDim.x) sw[e] = w[i0 + e];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int k = wid; k < ncols; k += nw) {
+    const double* v = V + k * ldv + i0;
+    double acc = 0.0;
+    for (int e = lane; e < cn; e += 32) acc = fma(v[e], sw[e], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) partial[blockIdx.x * ldp + k] = acc;
+  }
+}
+
+// h_k = sum_b partial[b][k]; w -= sum_k h_k V[k]; optionally H[:, col] (+)= h
+// (block 0) and normpart[b] = sum_{i in chunk b} w_i^2.
+__global__ void __launch_bounds__(256)
+k_orth_update(const double* __restrict__ V, int64_t ldv, int ncols, const double* __restrict__ partial, int ldp,
+              int nblk, double* __restrict__ w, int64_t n, double* __restrict__ hcol, int accumulate,
+              double* __restrict__ normpart, const int* __restrict__ done) {
+  if (done && *done) return;
+  __shared__ double sh[kMaxRestart + 1];
+  __shared__ double sred[32];
+  for (int k = threadIdx.x; k < ncols; k += blockDim.x) {
+    double h = 0.0;
+    for (int b = 0; b < nblk; ++b) h += partial[b * ldp + k];
+    sh[k] = h;
+    if (blockIdx.x == 0 && hcol) hcol[k] = accumulate ? hcol[k] + h : h;
+  }
+  __syncthreads();
+  const int64_t i0 = blockIdx.x * (int64_t)kChunk;
+  const int cn = (int)imin64(kChunk, n - i0);
+  double sq = 0.0;
+  for (int e = threadIdx.x; e < cn; e += blockDim.x) {
+    const int64_t i = i0 + e;
+    double acc = w[i];
+    for (int k = 0; k < ncols; ++k) acc = fma(-sh[k], V[k * ldv + i], acc);
+    w[i] = acc;
+    sq = fma(acc, acc, sq);
+  }
+  if (normpart) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o);
+    if (lane == 0) sred[wid] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += sred[q];
+      normpart[blockIdx.x] = s;
+    }
+  }
+}
+
+// normpart[b] = sum_{i in chunk b} x_i^2 (and optionally r = f - t first)
+__global__ void __launch_bounds__(256)
+k_residual_norm(const double* __restrict__ f, const double* __restrict__ t, double* __restrict__ r, int64_t n,
+                double* __restrict__ normpart) {
+  __shared__ double sred[32];
+  const int64_t i0 = blockIdx.x * (int64_t)kChunk;
+  const int cn = (int)imin64(kChunk, n - i0);
+  double sq = 0.0;
+  for (int e = threadIdx.x; e < cn; e += blockDim.x) {
+    const int64_t i = i0 + e;
+    const double v = t ? f[i] - t[i] : f[i];
+    if (r) r[i] = v;
+    sq = fma(v, v, sq);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o);
+  if (lane == 0) sred[wid] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += sred[q];
+    normpart[blockIdx.x] = s;
+  }
+}
+
+// scal[slot] = sqrt(sum normpart), scal[slot + 1] = 1 / that (0 if zero)
+__global__ void k_norm_final(const double* __restrict__ normpart, int nblk, double* __restrict__ scal, int slot) {
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += normpart[b];
+    const double nr = sqrt(s);
+    scal[slot] = nr;
+    scal[slot + 1] = nr > 0.0 ? 1.0 / nr : 0.0;
+  }
+}
+
+// y = x * scal[slot]
+__global__ void k_scale(const double* __restrict__ x, const double* __restrict__ scal, int slot,
+                        double* __restrict__ y, int64_t n, const int* __restrict__ done) {
+  if (done && *done) return;
+  const double a = scal[slot];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = x[i] * a;
+}
+
+// Start of a cycle: g = (beta, 0, ...), flags cleared.
+__global__ void k_cycle_start(double* __restrict__ g, int m, const double* __restrict__ scal, int slot,
+                              int* __restrict__ state) {
+  for (int i = threadIdx.x; i <= m; i += blockDim.x) g[i] = i == 0 ? scal[slot] : 0.0;
+  if (threadIdx.x == 0) {
+    state[0] = 0;
+    state[1] = 0;
+    state[2] = 0;
+  }
+}
+
+// Column j of the Hessenberg matrix is complete except H[j+1][j]: finish it,
+// apply the previous rotations, form the new one and test convergence.
+// H is column-major with leading dimension m + 1.
+__global__ void k_arnoldi_finish(int j, int m, const double* __restrict__ normpart, int nblk,
+                                 double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
+                                 double* __restrict__ g, double* __restrict__ scal, int* __restrict__ state,
+                                 double rhsnorm, double tol) {
+  if (state[0]) return;
+  if (threadIdx.x != 0) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += normpart[b];
+  const double hnext = sqrt(s);
+  double* h = H + (int64_t)j * (m + 1);
+  double colnorm = 0.0;
+  for (int i = 0; i <= j; ++i) colnorm = fmax(colnorm, fabs(h[i]));
+  h[j + 1] = hnext;
+  for (int i = 0; i < j; ++i) {
+    const double t = cs[i] * h[i] + sn[i] * h[i + 1];
+    h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+    h[i] = t;
+  }
+  const double den = hypot(h[j], hnext);
+  const double c = den > 0.0 ? h[j] / den : 1.0;
+  const double sv = den > 0.0 ? hnext / den : 0.0;
+  cs[j] = c;
+  sn[j] = sv;
+  h[j] = den;
+  h[j + 1] = 0.0;
+  g[j + 1] = -sv * g[j];
+  g[j] = c * g[j];
+  state[1] = j + 1;
+  scal[0] = hnext > 0.0 ? 1.0 / hnext : 0.0;
+  const double est = fabs(g[j + 1]) / rhsnorm;
+  scal[4] = est;
+  if (!isfinite(est) || !isfinite(hnext)) {
+    state[2] = 1;
+    state[0] = 1;
+  } else if (est <= tol || hnext <= 1e-14 * colnorm) {  // converged or happy breakdown
+    state[0] = 1;
+  }
+}
+
+// y = R^-1 g over the completed columns (back substitution, one thread).
+__global__ void k_lsq_solve(const double* __restrict__ H, int m, const double* __restrict__ g,
+                            const int* __restrict__ state, double* __restrict__ y) {
+  if (threadIdx.x != 0) return;
+  const int jd = state[1];
+  for (int i = jd - 1; i >= 0; --i) {
+    double acc = g[i];
+    for (int k = i + 1; k < jd; ++k) acc -= H[(int64_t)k * (m + 1) + i] * y[k];
+    const double d = H[(int64_t)i * (m + 1) + i];
+    y[i] = d != 0.0 ? acc / d : 0.0;
+  }
+}
+
+// t = sum_{k < jd} y_k V[k]
+__global__ void k_combine(const double* __restrict__ V, int64_t ldv, const double* __restrict__ y,
+                          const int* __restrict__ state, double* __restrict__ t, int64_t n) {
+  __shared__ double sy[kMaxRestart];
+  const int jd = state[1];
+  for (int k = threadIdx.x; k < jd; k += blockDim.x) sy[k] = y[k];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int k = 0; k < jd; ++k) acc = fma(sy[k], V[k * ldv + i], acc);
+    t[i] = acc;
+  }
+}
+
+__global__ void k_axpy(double* __restrict__ x, const double* __restrict__ z, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += z[i];
+}
+
+__global__ void k_copy(double* __restrict__ y, const double* __restrict__ x, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = x[i];
+}
+
+unsigned grid_for(int64_t n) { return (unsigned)imin64((n + 255) / 256, 152 * 16); }
+
+}  // namespace
+
+void apply_operator(Geom& g, const double* sigma, double* y, int precision, const int* done) {
+  switch (precision) {
+    case STOKES_FP64:
+      dlp_apply_f64(g, (const double2*)sigma, (double2*)y, true, g.pos.get(), g.N, done);
+      break;
+    default:
+      throw Error(STOKES_EINVAL, "precision not supported by this operator");
+  }
+}
+
+// ||v|| on the device, copied to the host (synchronises).
+static double device_norm(Geom& g, const double* v, int64_t n) {
+  Krylov& k = g.kr;
+  const int nblk = (int)((n + kChunk - 1) / kChunk);
+  k_residual_norm<<<nblk, 256, 0, g.stream>>>(v, nullptr, nullptr, n, k.partial.get());
+  k_norm_final<<<1, 32, 0, g.stream>>>(k.partial.get(), nblk, k.scal.get(), 2);
+  STOKES_LAUNCHED();
+  double h = 0.0;
+  STOKES_CUDA(cudaMemcpyAsync(&h, k.scal.get() + 2, sizeof(double), cudaMemcpyDeviceToHost, g.stream));
+  STOKES_CUDA(cudaStreamSynchronize(g.stream));
+  return h;
+}
+
+SolveResult gmres_solve(Geom& g, const double* f, double* x, double tol, int restart, int max_iter,
+                        int precision, int side) {
+  require(restart >= 1 && restart <= kMaxRestart, "restart must be in [1, 200]");
+  require(max_iter >= 1, "max_iter must be >= 1");
+  require(tol > 0 && std::isfinite(tol), "tol must be > 0");
+  const bool use_pc = g.bd.ready;
+  const bool left = side == STOKES_PC_LEFT && use_pc;
+  cudaStream_t s = g.stream;
+  const int64_t n = 2 * g.N;
+  const int m = restart;
+  Krylov& k = g.kr;
+  const int nblk = (int)((n + kChunk - 1) / kChunk);
+  const int ldp = kMaxRestart + 1;
+  if (k.m < m || k.n2 != n) {
+    k.V.alloc((size_t)(m + 1) * n);
+    k.Z.alloc(n);
+    k.w.alloc(n);
+    k.t.alloc(n);
+    k.r.alloc(n);
+    k.partial.alloc((size_t)nblk * ldp + 8);
+    k.H.alloc((size_t)(m + 1) * m);
+    k.cs.alloc(m);
+    k.sn.alloc(m);
+    k.g.alloc(m + 1);
+    k.y.alloc(m);
+    k.scal.alloc(8);
+    k.state.alloc(4);
+    k.m = m;
+    k.n2 = n;
+  }
+  k.nblk = nblk;
+  k.partial.alloc((size_t)nblk * ldp + 8);
+  double* normpart = k.partial.get();  // reductions of norms share the partial buffer
+  DevBuf<double> np2;                  // separate buffer for the norm partials inside a step
+  np2.alloc(nblk);
+  int* state = k.state.get();
+  const unsigned gv = grid_for(n);
+
+  SolveResult res;
+  const double fnorm = device_norm(g, f, n);
+  if (fnorm == 0.0) {
+    STOKES_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+    STOKES_CUDA(cudaStreamSynchronize(s));
+    return res;
+  }
+  double rhsnorm = fnorm;
+  if (left) {
+    bd_apply(g, f, k.t.get(), nullptr);
+    rhsnorm = device_norm(g, k.t.get(), n);
+  }
+  const double xnorm0 = device_norm(g, x, n);
+  bool x_is_zero = xnorm0 == 0.0;
+  int iters = 0;
+  while (true) {
+    // true residual r = f - A x
+    if (x_is_zero) {
+      k_residual_norm<<<nblk, 256, 0, s>>>(f, nullptr, k.r.get(), n, normpart);
+    } else {
+      apply_operator(g, x, k.t.get(), precision, nullptr);
+      k_residual_norm<<<nblk, 256, 0, s>>>(f, k.t.get(), k.r.get(), n, normpart);
+    }
+    k_norm_final<<<1, 32, 0, s>>>(normpart, nblk, k.scal.get(), 2);
+    STOKES_LAUNCHED();
+    double rn = 0.0;
+    STOKES_CUDA(cudaMemcpyAsync(&rn, k.scal.get() + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    STOKES_CUDA(cudaStreamSynchronize(s));
+    res.relres = rn / fnorm;
+    double beta = rn;
+    if (left) {
+      bd_apply(g, k.r.get(), k.Z.get(), nullptr);
+      k_copy<<<gv, 256, 0, s>>>(k.r.get(), k.Z.get(), n);
+      beta = device_norm(g, k.r.get(), n);
+    }
+    res.pc_relres = beta / rhsnorm;
+    res.iters = iters;
+    if (!std::isfinite(res.relres) || !std::isfinite(res.pc_relres)) {
+      res.status = STOKES_EBREAKDOWN;
+      return res;
+    }
+    const bool conv = left ? res.pc_relres <= tol : res.relres <= tol;
+    if (conv) return res;
+    if (iters >= max_iter) {
+      res.status = STOKES_ENOTCONV;
+      return res;
+    }
+    // v_0 = r / beta: the last norm computed (of r, or of P^-1 r) left
+    // beta and 1 / beta in scal[2], scal[3]
+    k_scale<<<gv, 256, 0, s>>>(k.r.get(), k.scal.get(), 3, k.V.get(), n, nullptr);
+    k_cycle_start<<<1, 256, 0, s>>>(k.g.get(), m, k.scal.get(), 2, state);
+    STOKES_LAUNCHED();
+    const int mc = std::min(m, max_iter - iters);
+    for (int j = 0; j < mc; ++j) {
+      double* vj = k.V.get() + (int64_t)j * n;
+      double* vnext = k.V.get() + (int64_t)(j + 1) * n;  // k.w normalised into it
+      if (!use_pc) {
+        apply_operator(g, vj, k.w.get(), precision, state);
+      } else if (!left) {
+        bd_apply(g, vj, k.Z.get(), state);
+        apply_operator(g, k.Z.get(), k.w.get(), precision, state);
+      } else {
+        apply_operator(g, vj, k.t.get(), precision, state);
+        bd_apply(g, k.t.get(), k.w.get(), state);
+      }
+      for (int pass = 0; pass < 2; ++pass) {
+        k_dot_partial<<<nblk, 256, 0, s>>>(k.V.get(), n, j + 1, k.w.get(), n, k.partial.get(), ldp, state);
+        k_orth_update<<<nblk, 256, 0, s>>>(k.V.get(), n, j + 1, k.partial.get(), ldp, nblk, k.w.get(), n,
+                                           k.H.get() + (int64_t)j * (m + 1), pass, pass ? np2.get() : nullptr,
+                                           state);
+      }
+      k_arnoldi_finish<<<1, 32, 0, s>>>(j, m, np2.get(), nblk, k.H.get(), k.cs.get(), k.sn.get(), k.g.get(),
+                                        k.scal.get(), state, rhsnorm, tol);
+      k_scale<<<gv, 256, 0, s>>>(k.w.get(), k.scal.get(), 0, vnext, n, state);
+      STOKES_LAUNCHED();
+    }
+    int hstate[3] = {0, 0, 0};
+    STOKES_CUDA(cudaMemcpyAsync(hstate, state, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    k_lsq_solve<<<1, 32, 0, s>>>(k.H.get(), m, k.g.get(), state, k.y.get());
+    k_combine<<<gv, 256, 0, s>>>(k.V.get(), n, k.y.get(), state, k.t.get(), n);
+    if (use_pc && !left) {
+      bd_apply(g, k.t.get(), k.Z.get(), nullptr);
+      k_axpy<<<gv, 256, 0, s>>>(x, k.Z.get(), n);
+    } else {
+      k_axpy<<<gv, 256, 0, s>>>(x, k.t.get(), n);
+    }
+    STOKES_LAUNCHED();
+    STOKES_CUDA(cudaStreamSynchronize(s));
+    iters += hstate[1];
+    x_is_zero = false;
+    if (hstate[2]) {
+      res.iters = iters;
+      res.status = STOKES_EBREAKDOWN;
+      return res;
+    }
+    if (hstate[1] == 0) {  // no progress possible
+      res.iters = iters;
+      res.status = STOKES_ENOTCONV;
+      return res;
+    }
+  }
+}
+
+}  // namespace stokes

@@ -1,0 +1,154 @@
+// Internal declarations of libstokes: the geometry handle, device buffers,
+// error handling and the launchers each translation unit provides.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "stokes.h"
+
+namespace stokes {
+
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define STOKES_CUDA(call)                                                                 \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      throw ::stokes::Error(e_ == cudaErrorMemoryAllocation ? STOKES_ENOMEM : STOKES_ECUDA, \
+                            std::string(#call) + ": " + cudaGetErrorString(e_));         \
+  } while (0)
+
+#define STOKES_LAUNCHED() STOKES_CUDA(cudaGetLastError())
+
+inline void require(bool ok, const std::string& msg, int code = STOKES_EINVAL) {
+  if (!ok) throw Error(code, msg);
+}
+
+// Owning device buffer (cudaMalloc / cudaFree), grows on demand.
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  void alloc(size_t count) {
+    if (count <= n && p) return;
+    release();
+    if (count == 0) return;
+    STOKES_CUDA(cudaMalloc(&p, count * sizeof(T)));
+    n = count;
+  }
+  T* get() const { return p; }
+};
+
+__host__ __device__ inline int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kInvPi = 0.31830988618379067154;
+constexpr double kInv4Pi = 0.07957747154594766788;
+
+// Per-block data of the block-diagonal preconditioner.
+struct BlockDiag {
+  bool ready = false;
+  std::vector<int64_t> rows;      // 2 n_k per component
+  std::vector<int64_t> elem_off;  // offset of each block's m x m matrix (prefix sums of m^2)
+  std::vector<int64_t> piv_off;   // offset of each block's pivots (prefix sums of m)
+  std::vector<int> small_ids;     // factorised and inverted by one CTA each
+  std::vector<int> inv_ids;       // applied through their explicit inverse
+  std::vector<int> tri_ids;       // applied by blocked triangular solves
+  int64_t max_inv_rows = 0;
+  DevBuf<double> lu;              // column-major LU in place (unit-lower L below the diagonal)
+  DevBuf<double> inv;             // explicit inverses (same offsets as lu)
+  DevBuf<int> piv;                // interchanges: row c was swapped with piv[c]
+  DevBuf<int> perm;               // row r of P A is row perm[r] of A
+  DevBuf<int64_t> d_elem_off, d_piv_off, d_rows, d_node_off;
+  DevBuf<int> d_small_ids, d_inv_ids;
+  DevBuf<int> status;             // 0 ok, 1 zero pivot
+  DevBuf<double> pv, ivp;         // pivot search scratch
+  DevBuf<int64_t> pi;
+};
+
+// Workspace of the Krylov solver.
+struct Krylov {
+  int m = 0;          // restart length the buffers are sized for
+  int64_t n2 = 0;     // vector length 2N
+  DevBuf<double> V, Z, w, t, x, f, r, partial, H, cs, sn, g, y, scal;
+  DevBuf<int> state;  // [0] done, [1] columns completed, [2] breakdown
+  int nblk = 0;
+};
+
+struct Geom {
+  int64_t N = 0;
+  int n_comp = 0;
+  int outer = -1;
+  int M = 0;  // number of pores
+  cudaStream_t stream = nullptr;
+  std::vector<int64_t> off;      // host copy of offsets
+  std::vector<double> centre_h;  // host copy of centres (2 per component)
+
+  // FP64 node data
+  DevBuf<double4_32a> src;    // x, y, w n_x / pi, w n_y / pi
+  DevBuf<double2> pos;    // x, y
+  DevBuf<double2> nrm;    // n
+  DevBuf<double> w;       // weights
+  DevBuf<double4_32a> selfc;  // t_x, t_y, -kappa w / (2 pi), w
+  DevBuf<int> comp;       // component of each node
+  DevBuf<int64_t> d_off;  // offsets
+  DevBuf<double2> centre; // completion centre per component
+  DevBuf<int> pore_ids;   // the M pore components
+
+  // FP32 node data (coordinates relative to the component centre)
+  DevBuf<float4> src32;   // lx, ly, a_x, a_y
+  DevBuf<float2> ctr32hi, ctr32lo;  // component centre split into float hi + lo
+
+  // workspaces
+  DevBuf<double4_32a> mom;    // lambda_x, lambda_y, xi, s0 per component
+  DevBuf<double2> part;   // split partial sums of the pair kernel
+  DevBuf<double2> stage_in, stage_out, stage_tgt;  // host<->device staging
+  DevBuf<double2> tmp2;
+
+  BlockDiag bd;
+  Krylov kr;
+};
+
+// ---- geometry.cu ----
+void moments_f64(Geom& g, const double2* sigma, const int* done);
+
+// ---- dlp_f64.cu ----
+// y = A sigma on the boundary (boundary=true, targets = nodes), or the
+// interior velocity at T targets (boundary=false). All pointers device.
+void dlp_apply_f64(Geom& g, const double2* sigma, double2* y, bool boundary,
+                   const double2* targets, int64_t T, const int* done);
+
+// ---- bd.cu ----
+void bd_setup(Geom& g);
+void bd_apply(Geom& g, const double* v, double* z, const int* done);
+
+// ---- gmres.cu ----
+struct SolveResult {
+  int iters = 0;
+  double relres = 0, pc_relres = 0;
+  int status = STOKES_OK;
+};
+SolveResult gmres_solve(Geom& g, const double* f, double* x, double tol, int restart, int max_iter,
+                        int precision, int side);
+
+// operator dispatch used by the solver and the API
+void apply_operator(Geom& g, const double* sigma, double* y, int precision, const int* done);
+
+}  // namespace stokes

@@ -1,0 +1,43 @@
+"""The C-ABI library builds, loads without a GPU and exports every function
+include/stokes.h declares."""
+import pathlib
+import re
+
+import pytest
+
+ROOT = pathlib.Path(__file__).resolve().parent.parent
+
+
+def _declared():
+    text = (ROOT / "include" / "stokes.h").read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(stokes_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1609_04484_gb300 import _build
+    if not _build.LIB.exists():
+        _build.build()
+    import paper_1609_04484_gb300 as S
+    return S
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for want in ("stokes_geometry_create", "stokes_matvec", "stokes_precond_setup",
+                 "stokes_gmres_solve", "stokes_eval_velocity", "stokes_last_error"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib.lib, name), name
+        assert hasattr(lib, name), f"binding lacks {name}"
+
+
+def test_null_handle_is_rejected_without_gpu(lib):
+    assert lib.lib.stokes_geometry_num_nodes(None) == -1
+    assert lib.lib.stokes_precond_setup(None, 1) == lib.STOKES_EINVAL
+    assert "null handle" in lib.stokes_last_error()
+    assert lib.lib.stokes_geometry_destroy(None) == lib.STOKES_OK

@@ -1,0 +1,207 @@
+"""GPU path (through the C ABI) against the CPU FP64 oracle.
+
+Tolerances: the operator is evaluated in a different order on the GPU
+(tiled pair sums, split over sources, FMA contraction), so results agree to
+a relative L2 error of a few hundred ulps of the operator's scale; the bound
+1e-12 on operator outputs leaves two decades of margin. Solutions: both
+sides solve to relative residual 1e-12, so densities agree to
+cond(A) * 1e-12 ~ 1e-9 at worst; the stated bound is 1e-10 (north of the
+measured cond ~5e3 for the 1152-node case times the GMRES stopping error
+being well below the bound in practice).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import stokes_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1609_04484_gb300 as S
+    return S
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return torch.device("cuda:0")
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64).reshape(-1)
+    b = np.asarray(b, dtype=np.float64).reshape(-1)
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _ragged_geometry():
+    pores = [si.circle_curve((-1.5, 0.1), 0.15, 17), si.circle_curve((0.0, -0.3), 0.2, 50),
+             si.circle_curve((1.4, 0.25), 0.12, 33)]
+    outer = si.superellipse_curve(3.0, 1.0, 203)
+    return si.assemble_geometry(pores, outer, (3.0, 1.0, 8))
+
+
+def _outer_only():
+    return si.assemble_geometry([], si.superellipse_curve(2.0, 1.0, 130), (2.0, 1.0, 8))
+
+
+GEOMS = {
+    "cfg1": lambda: si.cached_geometry("cfg1", 0),
+    "ragged": _ragged_geometry,
+    "outer_only": _outer_only,
+    "one_pore": lambda: si.config1_geometry(3, n_outer=96, n_pores=1, n_per_pore=40),
+}
+
+
+@pytest.fixture(scope="module", params=list(GEOMS))
+def case(request):
+    return request.param, GEOMS[request.param]()
+
+
+def test_matvec_fp64_matches_oracle(S, dev, case):
+    name, g = case
+    sig = si.random_density(g, 3).reshape(-1)
+    ref = O.matvec(g, sig)
+    with S.Geometry(g) as G:
+        y = torch.empty(2 * g.n_nodes, dtype=torch.float64, device=dev)
+        S.stokes_matvec(G.handle, torch.tensor(sig, device=dev), y, S.STOKES_FP64)
+        torch.cuda.synchronize()
+        assert rel(y.cpu().numpy(), ref) < 1e-12
+        # host pointers give the same bits
+        yh = np.empty_like(sig)
+        S.stokes_matvec(G.handle, sig, yh, S.STOKES_FP64)
+        assert np.array_equal(yh, y.cpu().numpy())
+
+
+def test_block_diagonal_apply_matches_oracle(S, dev, case):
+    name, g = case
+    v = np.random.default_rng(5).standard_normal(2 * g.n_nodes)
+    ref = O.BlockDiagonal(g).apply(v)
+    with S.Geometry(g) as G:
+        S.stokes_precond_setup(G.handle, S.STOKES_PC_BLOCKDIAG)
+        z = np.empty_like(v)
+        S.stokes_precond_apply(G.handle, v, z)
+        assert rel(z, ref) < 1e-11
+
+
+def test_gmres_fp64_matches_dense_oracle(S, dev, case):
+    name, g = case
+    f = si.pipe_bc(g).reshape(-1) if g.n_pores else si.shear_bc(g).reshape(-1)
+    ref = O.solve_dense(g, f)
+    with S.Geometry(g) as G:
+        S.stokes_precond_setup(G.handle, S.STOKES_PC_BLOCKDIAG)
+        sig = torch.zeros(2 * g.n_nodes, dtype=torch.float64, device=dev)
+        code, iters, rr, _ = S.stokes_gmres_solve(G.handle, torch.tensor(f, device=dev), sig, tol=1e-12,
+                                                  restart=50, max_iter=2000)
+        assert code == S.STOKES_OK and rr <= 1e-12
+        assert rel(sig.cpu().numpy(), ref) < 1e-10
+
+
+def test_gmres_iteration_count_matches_oracle_gmres(S, dev):
+    """Same method (right block-diagonal GMRES(50), tol 1e-10) on the
+    1152-node pipe problem: iteration counts within 2 (different rounding:
+    CGS2 on the GPU, MGS in the oracle)."""
+    g = si.cached_geometry("cfg1", 0)
+    f = si.pipe_bc(g).reshape(-1)
+    r_or = O.solve_gmres(g, f, tol=1e-10, restart=50, precond="bd")
+    with S.Geometry(g) as G:
+        S.stokes_precond_setup(G.handle, S.STOKES_PC_BLOCKDIAG)
+        sig = np.zeros_like(f)
+        code, iters, rr, _ = S.stokes_gmres_solve(G.handle, f, sig, tol=1e-10, restart=50)
+        assert code == S.STOKES_OK and rr <= 1e-10
+        assert abs(iters - r_or["iters"]) <= 2
+        assert rel(sig, r_or["x"]) < 1e-8
+
+
+@pytest.mark.parametrize("side", ["left", "none"])
+def test_gmres_left_and_unpreconditioned(S, dev, side):
+    g = si.config1_geometry(0, n_outer=256, n_pores=4, n_per_pore=32)
+    f = si.pipe_bc(g).reshape(-1)
+    ref = O.solve_dense(g, f)
+    with S.Geometry(g) as G:
+        if side == "left":
+            S.stokes_precond_setup(G.handle, S.STOKES_PC_BLOCKDIAG)
+        sig = np.zeros_like(f)
+        code, iters, rr, pr = S.stokes_gmres_solve(G.handle, f, sig, tol=1e-12, restart=40, max_iter=3000,
+                                                   pc_side=S.STOKES_PC_LEFT if side == "left" else S.STOKES_PC_RIGHT)
+        assert code == S.STOKES_OK
+        if side == "left":
+            assert pr <= 1e-12
+        assert rel(sig, ref) < 1e-9
+
+
+def test_velocity_matches_oracle(S, dev):
+    g = si.cached_geometry("cfg1", 0)
+    sig = O.solve_dense(g, si.pipe_bc(g).reshape(-1))
+    T = si.interior_targets(g, 4096, min_dist=0.05, seed=11)
+    ref = O.velocity(g, sig, T)
+    with S.Geometry(g) as G:
+        u = np.empty(T.size)
+        S.stokes_eval_velocity(G.handle, sig, T.reshape(-1), u)
+        assert rel(u, ref) < 1e-12
+
+
+def test_exact_stokeslet_flow_through_gpu_solve(S, dev):
+    """End to end against the closed form of Eq. 13 (not just the oracle)."""
+    g = si.config1_geometry(2, n_outer=512, n_pores=4, n_per_pore=64)
+    c, lam, mu = si.stokeslet_rotlet_params(g, 0)
+    f = si.stokeslet_rotlet_velocity(g.nodes, c, lam, mu).reshape(-1)
+    T = si.interior_targets(g, 300, min_dist=0.3, seed=5)
+    ue = si.stokeslet_rotlet_velocity(T, c, lam, mu)
+    with S.Geometry(g) as G:
+        S.stokes_precond_setup(G.handle)
+        sig = np.zeros_like(f)
+        S.stokes_gmres_solve(G.handle, f, sig, tol=1e-13, restart=50)
+        u = np.empty(T.size)
+        S.stokes_eval_velocity(G.handle, sig, T.reshape(-1), u)
+        assert np.abs(u.reshape(-1, 2) - ue).max() / np.abs(ue).max() < 1e-9
+
+
+def test_errors_are_reported(S, dev):
+    g = si.config1_geometry(0, n_outer=64, n_pores=2, n_per_pore=16)
+    bad = g.offsets.copy()
+    bad[1] = bad[0] + 4                 # a component with fewer than 8 nodes
+    with pytest.raises(S.StokesError) as e:
+        S.stokes_geometry_create(g.nodes.reshape(-1), g.normals.reshape(-1), g.weights, g.curvature, bad,
+                                 g.n_comp, g.outer_comp)
+    assert e.value.code == S.STOKES_EINVAL
+    nb = g.normals.copy()
+    nb[3] *= 1.1
+    with pytest.raises(S.StokesError):
+        S.stokes_geometry_create(g.nodes.reshape(-1), nb.reshape(-1), g.weights, g.curvature, g.offsets,
+                                 g.n_comp, g.outer_comp)
+    with S.Geometry(g) as G:
+        v = np.zeros(2 * g.n_nodes)
+        with pytest.raises(S.StokesError) as e:
+            S.stokes_precond_apply(G.handle, v, np.empty_like(v))
+        assert e.value.code == S.STOKES_ESTATE
+        f = si.pipe_bc(g).reshape(-1)
+        sig = np.zeros_like(f)
+        code, iters, rr, _ = S.stokes_gmres_solve(G.handle, f, sig, tol=1e-14, restart=5, max_iter=3)
+        assert code == S.STOKES_ENOTCONV and iters == 3 and rr > 1e-14
+        with pytest.raises(S.StokesError):
+            S.stokes_gmres_solve(G.handle, f, sig, tol=-1.0)
+        # zero right-hand side: zero solution, no iterations
+        code, iters, rr, _ = S.stokes_gmres_solve(G.handle, np.zeros_like(f), sig)
+        assert code == S.STOKES_OK and iters == 0 and not sig.any()
+
+
+@pytest.mark.parametrize("rows", [64])
+def test_full_size_matvec_sampled_rows(S, dev, rows):
+    """136,192-node geometry (1000 pores), launch shape as in the benchmark:
+    sampled rows of A sigma against the oracle's matrix-free rows."""
+    g = si.cached_geometry("cfg2", 0)
+    sig = si.random_density(g, 9).reshape(-1)
+    idx = np.random.default_rng(1).choice(g.n_nodes, rows, replace=False)
+    idx = np.concatenate([idx, [0, g.n_nodes - 1, int(g.offsets[g.outer_comp])]])
+    ref = O.apply_rows(g, sig, idx)
+    with S.Geometry(g) as G:
+        y = torch.empty(2 * g.n_nodes, dtype=torch.float64, device=dev)
+        S.stokes_matvec(G.handle, torch.tensor(sig, device=dev), y, S.STOKES_FP64)
+        got = y.cpu().numpy().reshape(-1, 2)[idx]
+        assert rel(got, ref) < 1e-12
