@@ -16,9 +16,10 @@ def _declared():
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_1609_04484_gb300 import _build
-    if not _build.LIB.exists():
-        _build.build()
+    import __graft_entry__
+    b = __graft_entry__._build_module()
+    if not b.LIB.exists():
+        b.build()
     import paper_1609_04484_gb300 as S
     return S
 
