@@ -63,8 +63,10 @@ enum stokes_status {
 
 /* Arithmetic of the discrete operator.
  * STOKES_FP64: native double precision everywhere.
- * STOKES_FP32: single precision pair sums (node coordinates taken relative to
- *   their component's centre), double-precision moments and outputs.
+ * STOKES_FP32: single-precision pair sums and completion (positions split
+ *   into float hi + lo parts so that differences of nearby nodes keep single
+ *   precision relative to their distance), double-precision diagonal terms,
+ *   moments and outputs.
  * STOKES_DF64: double-float pair sums (unevaluated sums of two floats with
  *   error-free transformations) giving FP64-class accuracy on the FP32 pipes.
  * STOKES_MIXED_IR (solve only): FP32 inner GMRES inside FP64 iterative
@@ -132,10 +134,14 @@ int stokes_precond_apply(stokes_geom* g, const double* v, double* z);
  * stokes_precond_setup call (none if never set up).
  *   f       [2N] right-hand side (the boundary data at the nodes)
  *   tol     relative residual tolerance (> 0)
- *   restart Krylov dimension per cycle, 1..200
+ *   restart Krylov dimension per cycle, 1..1000
  *   max_iter total inner iterations (>= 1)
  *   precision STOKES_FP64, STOKES_DF64 (operator arithmetic; Arnoldi, Givens
  *             and the least-squares update always FP64) or STOKES_MIXED_IR
+ *             (iterative refinement: outer residual with the DF64 operator,
+ *             corrections by GMRES on the FP32 operator to relative
+ *             tolerance max(1e-5, tol / (2 |r| / |f|)); iters_out counts the
+ *             inner iterations, both residual outputs are the outer one)
  *   pc_side STOKES_PC_RIGHT (default; stops on the true residual
  *           |f - A sigma| / |f|) or STOKES_PC_LEFT (Sec. 4.1; stops on the
  *           preconditioned residual |P^-1 (f - A sigma)| / |P^-1 f|)
@@ -156,6 +162,32 @@ int stokes_gmres_solve(stokes_geom* g, const double* f, double tol, int restart,
  * A target on a node gives a non-finite value for that target. */
 int stokes_eval_velocity(stokes_geom* g, const double* sigma, const double* targets,
                          int64_t n_targets, double* u, int precision);
+
+/* Kernel timing. While enabled, the library brackets every launch of each
+ * kernel class below with CUDA events on the handle's stream; launches that
+ * a converged GMRES cycle skipped are dropped from the record.
+ * stokes_profile_enable(g, on) synchronises the stream, clears the record
+ * and switches recording on (on != 0) or off. stokes_profile_read
+ * synchronises and returns, for one class, the number of recorded launches,
+ * their summed device time in ms and their summed algorithmic work:
+ *   PAIRS_*    source-target pairs of the pair sum (all N x T pairs)
+ *   EPILOGUE   target-pore pairs of the completion
+ *   BD_APPLY   bytes: every block inverse / factor read once, v in, z out
+ *   ARNOLDI    bytes of one CGS2 step: 4 (j + 1) + 4 vectors of 2N doubles
+ *   BD_SETUP   flops: (2/3) m^3 per block, 2 m^3 where the inverse is formed
+ * Any output pointer may be NULL. */
+enum stokes_prof_kind {
+  STOKES_PROF_PAIRS_FP64 = 0,
+  STOKES_PROF_PAIRS_FP32 = 1,
+  STOKES_PROF_PAIRS_DF64 = 2,
+  STOKES_PROF_EPILOGUE = 3,
+  STOKES_PROF_BD_APPLY = 4,
+  STOKES_PROF_ARNOLDI = 5,
+  STOKES_PROF_BD_SETUP = 6
+};
+int stokes_profile_enable(stokes_geom* g, int on);
+int stokes_profile_read(stokes_geom* g, int kind, int64_t* launches, double* total_ms,
+                        double* total_units);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* stokes_last_error(void);

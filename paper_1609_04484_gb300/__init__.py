@@ -21,6 +21,9 @@ __all__ = [
     "StokesError", "lib", "library_path", "stokes_geometry_create", "stokes_geometry_destroy",
     "stokes_geometry_num_nodes", "stokes_matvec", "stokes_precond_setup", "stokes_precond_apply",
     "stokes_gmres_solve", "stokes_eval_velocity", "stokes_last_error", "Geometry",
+    "stokes_profile_enable", "stokes_profile_read", "STOKES_PROF_PAIRS_FP64", "STOKES_PROF_PAIRS_FP32",
+    "STOKES_PROF_PAIRS_DF64", "STOKES_PROF_EPILOGUE", "STOKES_PROF_BD_APPLY", "STOKES_PROF_ARNOLDI",
+    "STOKES_PROF_BD_SETUP",
 ]
 
 STOKES_OK, STOKES_EINVAL, STOKES_ENOMEM, STOKES_ECUDA = 0, -1, -2, -3
@@ -28,6 +31,8 @@ STOKES_ENOTCONV, STOKES_EBREAKDOWN, STOKES_ESTATE = -4, -5, -6
 STOKES_FP64, STOKES_FP32, STOKES_DF64, STOKES_MIXED_IR = 0, 1, 2, 3
 STOKES_PC_NONE, STOKES_PC_BLOCKDIAG = 0, 1
 STOKES_PC_RIGHT, STOKES_PC_LEFT = 0, 1
+(STOKES_PROF_PAIRS_FP64, STOKES_PROF_PAIRS_FP32, STOKES_PROF_PAIRS_DF64, STOKES_PROF_EPILOGUE,
+ STOKES_PROF_BD_APPLY, STOKES_PROF_ARNOLDI, STOKES_PROF_BD_SETUP) = range(7)
 
 _PKG = pathlib.Path(__file__).resolve().parent
 library_path = _PKG / "lib" / "libstokes.so"
@@ -55,6 +60,8 @@ def _load():
                                    ctypes.POINTER(D)]),
         "stokes_eval_velocity": (I, [P, P, P, I64, P, I]),
         "stokes_last_error": (ctypes.c_char_p, []),
+        "stokes_profile_enable": (I, [P, I]),
+        "stokes_profile_read": (I, [P, I, ctypes.POINTER(I64), ctypes.POINTER(D), ctypes.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -153,6 +160,20 @@ def stokes_eval_velocity(handle, sigma, targets, u, precision=STOKES_FP64):
     T = (targets.numel() if hasattr(targets, "numel") else targets.size) // 2
     _check(lib.stokes_eval_velocity(ctypes.c_void_p(handle), _ptr(sigma, count=n2), _ptr(targets, count=2 * T),
                                     ctypes.c_int64(T), _ptr(u, count=2 * T), int(precision)))
+
+
+def stokes_profile_enable(handle, on=True):
+    _check(lib.stokes_profile_enable(ctypes.c_void_p(handle), int(bool(on))))
+
+
+def stokes_profile_read(handle, kind):
+    """Returns (launches, total_ms, total_units) for one kernel class."""
+    n = ctypes.c_int64(0)
+    ms = ctypes.c_double(0.0)
+    u = ctypes.c_double(0.0)
+    _check(lib.stokes_profile_read(ctypes.c_void_p(handle), int(kind), ctypes.byref(n), ctypes.byref(ms),
+                                   ctypes.byref(u)))
+    return n.value, ms.value, u.value
 
 
 class Geometry:

@@ -184,14 +184,49 @@ int stokes_eval_velocity(stokes_geom* h, const double* sigma, const double* targ
     Geom& g = handle(h);
     stokes::require(sigma && targets && u, "null array argument");
     stokes::require(n_targets >= 0, "n_targets must be >= 0");
-    stokes::require(precision == STOKES_FP64, "precision must be FP64 for velocity evaluation");
+    stokes::require(precision == STOKES_FP64 || precision == STOKES_FP32 || precision == STOKES_DF64,
+                    "precision must be FP64, FP32 or DF64");
     if (n_targets == 0) return;
     const double* s = input_view(g, sigma, 2 * g.N, g.stage_in);
     const double* t = input_view(g, targets, 2 * n_targets, g.stage_tgt);
     bool staged;
     double* uo = output_view(g, u, 2 * n_targets, g.stage_out, staged);
-    stokes::dlp_apply_f64(g, (const double2*)s, (double2*)uo, false, (const double2*)t, n_targets, nullptr);
+    const auto* sv = (const double2*)s;
+    const auto* tv = (const double2*)t;
+    if (precision == STOKES_FP64) stokes::dlp_apply_f64(g, sv, (double2*)uo, false, tv, n_targets, nullptr);
+    else if (precision == STOKES_FP32) stokes::dlp_apply_f32(g, sv, (double2*)uo, false, tv, n_targets, nullptr);
+    else stokes::dlp_apply_df64(g, sv, (double2*)uo, false, tv, n_targets, nullptr);
     finish_output(g, u, uo, 2 * n_targets, staged);
+  });
+}
+
+int stokes_profile_enable(stokes_geom* h, int on) {
+  return guarded([&] {
+    Geom& g = handle(h);
+    STOKES_CUDA(cudaStreamSynchronize(g.stream));
+    g.prof.clear();
+    g.prof.on = on != 0;
+  });
+}
+
+int stokes_profile_read(stokes_geom* h, int kind, int64_t* launches, double* total_ms, double* total_units) {
+  return guarded([&] {
+    Geom& g = handle(h);
+    stokes::require(kind >= 0 && kind < stokes::kProfKinds, "unknown profile kind");
+    STOKES_CUDA(cudaStreamSynchronize(g.stream));
+    int64_t cnt = 0;
+    double ms = 0.0, units = 0.0;
+    for (const auto& e : g.prof.entries) {
+      if (e.kind != kind || !e.valid) continue;
+      float t = 0.f;
+      STOKES_CUDA(cudaEventElapsedTime(&t, e.a, e.b));
+      ++cnt;
+      ms += t;
+      units += e.units;
+    }
+    if (launches) *launches = cnt;
+    if (total_ms) *total_ms = ms;
+    if (total_units) *total_units = units;
   });
 }
 

@@ -480,6 +480,12 @@ void bd_setup(Geom& g) {
   BlockDiag& b = g.bd;
   b.ready = false;
   cudaStream_t s = g.stream;
+  double flops = 0.0;  // (2/3) m^3 for the LU, + 4/3 m^3 more where inverted
+  for (int k = 0; k < g.n_comp; ++k) {
+    const double m = 2.0 * (double)(g.off[k + 1] - g.off[k]);
+    flops += (m <= kInv ? 2.0 : 2.0 / 3.0) * m * m * m;
+  }
+  const int ps = g.prof.begin(kProfBdSetup, flops, s);
   const int nc = g.n_comp;
   b.rows.assign(nc, 0);
   b.elem_off.assign(nc + 1, 0);
@@ -585,6 +591,7 @@ void bd_setup(Geom& g) {
         b.lu.get() + b.elem_off[k], m, b.perm.get() + b.piv_off[k], b.inv.get() + b.elem_off[k]);
     STOKES_LAUNCHED();
   }
+  g.prof.end(ps, s);
   STOKES_CUDA(cudaStreamSynchronize(s));
   b.ready = true;
 }
@@ -593,6 +600,8 @@ void bd_apply(Geom& g, const double* v, double* z, const int* done) {
   BlockDiag& b = g.bd;
   require(b.ready, "preconditioner not set up", STOKES_ESTATE);
   cudaStream_t s = g.stream;
+  // algorithmic bytes: every block's inverse or factors once, v in, z out
+  const int pb = g.prof.begin(kProfBdApply, 8.0 * (double)b.elem_off[g.n_comp] + 32.0 * (double)g.N, s);
   if (!b.inv_ids.empty()) {
     dim3 grid((unsigned)b.inv_ids.size(), (unsigned)((b.max_inv_rows + 63) / 64));
     k_bd_gemv<<<grid, 256, b.max_inv_rows * sizeof(double), s>>>(
@@ -622,6 +631,7 @@ void bd_apply(Geom& g, const double* v, double* z, const int* done) {
     }
     STOKES_LAUNCHED();
   }
+  g.prof.end(pb, s);
 }
 
 }  // namespace stokes

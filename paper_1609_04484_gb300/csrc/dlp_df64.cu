@@ -1,0 +1,126 @@
+// Double-float double-layer operator: FP64-class accuracy on the FP32 pipes.
+//
+// On this GPU double precision issues at 1/64 of the single-precision rate,
+// so the pair sum is evaluated with unevaluated sums of two floats
+// (Dekker's double-length arithmetic: TwoSum, FastTwoSum and an FMA-based
+// TwoProduct). Positions, the weighted normals and the density are split
+// hi + lo; r, rho^2, r.a and r.sigma are formed with error-free
+// transformations, 1/rho^2 by one Newton step on a correctly rounded float
+// reciprocal, and the running sum of each tile keeps its rounding errors in
+// a second float (the compensated summation of Ogita, Rump and Oishi).
+// Tile sums are accumulated in double. The diagonal, jump, wall and
+// completion terms are FP64.
+#include "dlp_common.cuh"
+
+namespace stokes {
+
+namespace {
+
+using dlp::df32;
+
+constexpr int kTile = 128;
+constexpr int kThreads = 128;
+
+__device__ __forceinline__ void acc_prod(df32& acc, df32 c, df32 r) {
+  const float p = c.h * r.h;
+  float pe = fmaf(c.h, r.h, -p);
+  pe = fmaf(c.h, r.l, pe);
+  pe = fmaf(c.l, r.h, pe);
+  const df32 s = dlp::two_sum(acc.h, p);
+  acc.h = s.h;
+  acc.l += s.l + pe;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_dlp_pairs_df64(int64_t N, const float4* __restrict__ pos, const float4* __restrict__ aw,
+                 const double2* __restrict__ sig, int64_t T, const double2* __restrict__ tgt, int64_t chunk,
+                 int self_skip, double2* __restrict__ part, const int* __restrict__ done) {
+  if (done && *done) return;
+  __shared__ float4 s_p[kTile];  // x_hi, y_hi, x_lo, y_lo
+  __shared__ float4 s_a[kTile];  // a_x hi, a_y hi, a_x lo, a_y lo
+  __shared__ float4 s_s[kTile];  // sigma_x hi, sigma_y hi, sigma_x lo, sigma_y lo
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double2 x = make_double2(0.0, 0.0);
+  if (i < T) x = tgt[i];
+  const df32 X = dlp::df_from_double(x.x), Y = dlp::df_from_double(x.y);
+  const int64_t j0 = blockIdx.y * chunk;
+  const int64_t j1 = imin64(N, j0 + chunk);
+  const int64_t iself = self_skip ? i : -1;
+  double ux = 0.0, uy = 0.0;
+  for (int64_t t0 = j0; t0 < j1; t0 += kTile) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < kTile; q += blockDim.x) {
+      const int64_t j = t0 + q;
+      if (j < j1) {
+        const double2 sg = sig[j];
+        const df32 sx = dlp::df_from_double(sg.x), sy = dlp::df_from_double(sg.y);
+        s_p[q] = pos[j];
+        s_a[q] = aw[j];
+        s_s[q] = make_float4(sx.h, sy.h, sx.l, sy.l);
+      } else {
+        s_p[q] = make_float4(1e18f, 1e18f, 0.f, 0.f);
+        s_a[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        s_s[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    __syncthreads();
+    const int64_t jb = t0 - iself;
+    df32 ax = {0.f, 0.f}, ay = {0.f, 0.f};
+#pragma unroll 2
+    for (int q = 0; q < kTile; ++q) {
+      const float4 p = s_p[q];
+      const float4 a = s_a[q];
+      const float4 s = s_s[q];
+      df32 rx = dlp::two_diff(X.h, p.x);
+      rx.l += X.l - p.z;
+      df32 ry = dlp::two_diff(Y.h, p.y);
+      ry.l += Y.l - p.w;
+      // rho^2 = rx^2 + ry^2
+      const float px = rx.h * rx.h;
+      float ex = fmaf(rx.h, rx.h, -px);
+      ex = fmaf(rx.h + rx.h, rx.l, ex);
+      const float py = ry.h * ry.h;
+      float ey = fmaf(ry.h, ry.h, -py);
+      ey = fmaf(ry.h + ry.h, ry.l, ey);
+      df32 r2 = dlp::two_sum(px, py);
+      r2 = dlp::fast_two_sum(r2.h, r2.l + (ex + ey));
+      if (q + jb == 0) r2 = {1.f, 0.f};  // r = 0: the pair contributes 0
+      // 1 / rho^2: one Newton step from the correctly rounded reciprocal
+      const float y0 = __frcp_rn(r2.h);
+      float t = fmaf(-r2.h, y0, 1.0f);
+      t = fmaf(-r2.l, y0, t);
+      const df32 inv = {y0, y0 * t};
+      const df32 d = dlp::df_dot2(rx, ry, {a.x, a.z}, {a.y, a.w});
+      const df32 e = dlp::df_dot2(rx, ry, {s.x, s.z}, {s.y, s.w});
+      const df32 c = dlp::df_mul(dlp::df_mul(d, inv), dlp::df_mul(e, inv));
+      acc_prod(ax, c, rx);
+      acc_prod(ay, c, ry);
+    }
+    ux += dlp::df_to_double(ax);
+    uy += dlp::df_to_double(ay);
+  }
+  if (i < T) part[blockIdx.y * T + i] = make_double2(ux, uy);
+}
+
+}  // namespace
+
+void dlp_apply_df64(Geom& g, const double2* sigma, double2* y, bool boundary, const double2* targets, int64_t T,
+                    const int* done) {
+  if (T == 0) return;
+  moments_f64(g, sigma, done);
+  int splits;
+  int64_t chunk;
+  dlp::pair_launch_shape(g.N, T, kThreads, kTile, splits, chunk);
+  g.part.alloc((size_t)splits * T);
+  dim3 grid((unsigned)((T + kThreads - 1) / kThreads), (unsigned)splits);
+  const int pe = g.prof.begin(kProfPairsDF64, (double)g.N * (double)T, g.stream);
+  k_dlp_pairs_df64<<<grid, kThreads, 0, g.stream>>>(g.N, g.df_pos.get(), g.df_a.get(), sigma, T, targets, chunk,
+                                                     boundary ? 1 : 0, g.part.get(), done);
+  STOKES_LAUNCHED();
+  g.prof.end(pe, g.stream);
+  const int pq = g.prof.begin(kProfEpilogue, (double)g.M * (double)T, g.stream);
+  dlp::launch_epilogue<false>(g, T, splits, boundary, targets, sigma, y, done);
+  g.prof.end(pq, g.stream);
+}
+
+}  // namespace stokes

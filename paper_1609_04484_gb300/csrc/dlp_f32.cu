@@ -1,0 +1,98 @@
+// FP32 double-layer operator (inner solves of the mixed-precision
+// refinement). The pair sum runs in single precision; each node position is
+// stored as hi = fl32(x) plus lo = fl32(x - hi), and r = (x_i,hi - x_j,hi) +
+// (x_i,lo - x_j,lo) keeps the difference of nearby nodes accurate to single
+// precision relative to |r| (a plain float subtraction would lose up to
+// |x| / |r| of it). Per-tile float sums are accumulated in double; the
+// diagonal, jump and wall terms stay FP64, the completion runs in FP32.
+#include "dlp_common.cuh"
+
+namespace stokes {
+
+namespace {
+
+constexpr int kTile = 256;
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_dlp_pairs_f32(int64_t N, const float4* __restrict__ src, const float2* __restrict__ lo,
+                const double2* __restrict__ sig, int64_t T, const double2* __restrict__ tgt, int64_t chunk,
+                int self_skip, double2* __restrict__ part, const int* __restrict__ done) {
+  if (done && *done) return;
+  __shared__ float4 s_a[kTile];  // x_hi, y_hi, a_x, a_y
+  __shared__ float4 s_b[kTile];  // x_lo, y_lo, sigma_x, sigma_y
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double2 x = make_double2(0.0, 0.0);
+  if (i < T) x = tgt[i];
+  const float xh = (float)x.x, yh = (float)x.y;
+  const float xl = (float)(x.x - (double)xh), yl = (float)(x.y - (double)yh);
+  const int64_t j0 = blockIdx.y * chunk;
+  const int64_t j1 = imin64(N, j0 + chunk);
+  const int64_t iself = self_skip ? i : -1;
+  double ux = 0.0, uy = 0.0;
+  for (int64_t t0 = j0; t0 < j1; t0 += kTile) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < kTile; q += blockDim.x) {
+      const int64_t j = t0 + q;
+      if (j < j1) {
+        const float2 l = lo[j];
+        const double2 sg = sig[j];
+        s_a[q] = src[j];
+        s_b[q] = make_float4(l.x, l.y, (float)sg.x, (float)sg.y);
+      } else {
+        s_a[q] = make_float4(1e18f, 1e18f, 0.f, 0.f);
+        s_b[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    __syncthreads();
+    const int64_t jb = t0 - iself;
+    float fx = 0.f, fy = 0.f;
+#pragma unroll 8
+    for (int q = 0; q < kTile; ++q) {
+      const float4 a = s_a[q];
+      const float4 b = s_b[q];
+      const float rx = (xh - a.x) + (xl - b.x);
+      const float ry = (yh - a.y) + (yl - b.y);
+      float r2 = fmaf(rx, rx, ry * ry);
+      r2 = (q + jb == 0) ? 1.f : r2;
+      const float inv = rcp_approx(r2);
+      const float d = fmaf(rx, a.z, ry * a.w);
+      const float e = fmaf(rx, b.z, ry * b.w);
+      const float c = (d * inv) * (e * inv);
+      fx = fmaf(c, rx, fx);
+      fy = fmaf(c, ry, fy);
+    }
+    ux += fx;
+    uy += fy;
+  }
+  if (i < T) part[blockIdx.y * T + i] = make_double2(ux, uy);
+}
+
+}  // namespace
+
+void dlp_apply_f32(Geom& g, const double2* sigma, double2* y, bool boundary, const double2* targets, int64_t T,
+                   const int* done) {
+  if (T == 0) return;
+  moments_f64(g, sigma, done);
+  int splits;
+  int64_t chunk;
+  dlp::pair_launch_shape(g.N, T, kThreads, kTile, splits, chunk);
+  g.part.alloc((size_t)splits * T);
+  dim3 grid((unsigned)((T + kThreads - 1) / kThreads), (unsigned)splits);
+  const int pe = g.prof.begin(kProfPairsF32, (double)g.N * (double)T, g.stream);
+  k_dlp_pairs_f32<<<grid, kThreads, 0, g.stream>>>(g.N, g.f32_src.get(), g.f32_lo.get(), sigma, T, targets, chunk,
+                                                    boundary ? 1 : 0, g.part.get(), done);
+  STOKES_LAUNCHED();
+  g.prof.end(pe, g.stream);
+  const int pq = g.prof.begin(kProfEpilogue, (double)g.M * (double)T, g.stream);
+  dlp::launch_epilogue<true>(g, T, splits, boundary, targets, sigma, y, done);
+  g.prof.end(pq, g.stream);
+}
+
+}  // namespace stokes

@@ -64,23 +64,28 @@ __global__ void k_moments_f64(const double2* __restrict__ pos, const double2* __
   if (threadIdx.x == 0) mom[k] = acc;
 }
 
+__device__ __forceinline__ float2 split_f(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+
 __global__ void k_prep_nodes(int64_t N, const double2* __restrict__ pos, const double2* __restrict__ nrm,
                              const double* __restrict__ w, const double* __restrict__ kappa,
-                             const int* __restrict__ comp, const double2* __restrict__ centre,
-                             const float2* __restrict__ chi, double4_32a* __restrict__ src,
-                             double4_32a* __restrict__ selfc, float4* __restrict__ src32) {
+                             double4_32a* __restrict__ src, double4_32a* __restrict__ selfc,
+                             float4* __restrict__ f32_src, float2* __restrict__ f32_lo,
+                             float4* __restrict__ df_pos, float4* __restrict__ df_a) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   const double2 p = pos[i], n = nrm[i];
   const double wi = w[i];
-  src[i] = make_double4_32a(p.x, p.y, wi * n.x * kInvPi, wi * n.y * kInvPi);
+  const double ax = wi * n.x * kInvPi, ay = wi * n.y * kInvPi;
+  src[i] = make_double4_32a(p.x, p.y, ax, ay);
   selfc[i] = make_double4_32a(-n.y, n.x, -kappa[i] * wi / (2.0 * kPi), wi);
-  // FP32 copy: coordinates relative to the float-rounded component centre
-  const int k = comp[i];
-  const float2 ch = chi[k];
-  src32[i] = make_float4((float)(p.x - (double)ch.x), (float)(p.y - (double)ch.y),
-                         (float)(wi * n.x * kInvPi), (float)(wi * n.y * kInvPi));
-  (void)centre;
+  const float2 sx = split_f(p.x), sy = split_f(p.y), sax = split_f(ax), say = split_f(ay);
+  f32_src[i] = make_float4(sx.x, sy.x, sax.x, say.x);
+  f32_lo[i] = make_float2(sx.y, sy.y);
+  df_pos[i] = make_float4(sx.x, sy.x, sx.y, sy.y);
+  df_a[i] = make_float4(sax.x, say.x, sax.y, say.y);
 }
 
 }  // namespace
@@ -171,12 +176,6 @@ Geom* geometry_create(const double* nodes, const double* normals, const double* 
     std::vector<int> pores;
     for (int c = 0; c < n_comp; ++c)
       if (c != outer_comp) pores.push_back(c);
-    std::vector<float2> chi(n_comp), clo(n_comp);
-    for (int c = 0; c < n_comp; ++c) {
-      const float hxf = (float)g->centre_h[2 * c], hyf = (float)g->centre_h[2 * c + 1];
-      chi[c] = make_float2(hxf, hyf);
-      clo[c] = make_float2((float)(g->centre_h[2 * c] - hxf), (float)(g->centre_h[2 * c + 1] - hyf));
-    }
 
     g->pos.alloc(N);
     g->nrm.alloc(N);
@@ -185,13 +184,14 @@ Geom* geometry_create(const double* nodes, const double* normals, const double* 
     kap.alloc(N);
     g->src.alloc(N);
     g->selfc.alloc(N);
-    g->src32.alloc(N);
+    g->f32_src.alloc(N);
+    g->f32_lo.alloc(N);
+    g->df_pos.alloc(N);
+    g->df_a.alloc(N);
     g->comp.alloc(N);
     g->d_off.alloc(n_comp + 1);
     g->centre.alloc(n_comp);
     g->pore_ids.alloc(pores.size() ? pores.size() : 1);
-    g->ctr32hi.alloc(n_comp);
-    g->ctr32lo.alloc(n_comp);
     g->mom.alloc(n_comp);
     STOKES_CUDA(cudaMemcpyAsync(g->pos.get(), hx.data(), 16 * N, cudaMemcpyHostToDevice, s));
     STOKES_CUDA(cudaMemcpyAsync(g->nrm.get(), hn.data(), 16 * N, cudaMemcpyHostToDevice, s));
@@ -202,13 +202,11 @@ Geom* geometry_create(const double* nodes, const double* normals, const double* 
     STOKES_CUDA(cudaMemcpyAsync(g->centre.get(), g->centre_h.data(), 16 * n_comp, cudaMemcpyHostToDevice, s));
     if (!pores.empty())
       STOKES_CUDA(cudaMemcpyAsync(g->pore_ids.get(), pores.data(), 4 * pores.size(), cudaMemcpyHostToDevice, s));
-    STOKES_CUDA(cudaMemcpyAsync(g->ctr32hi.get(), chi.data(), 8 * n_comp, cudaMemcpyHostToDevice, s));
-    STOKES_CUDA(cudaMemcpyAsync(g->ctr32lo.get(), clo.data(), 8 * n_comp, cudaMemcpyHostToDevice, s));
     const int tb = 256;
     k_prep_nodes<<<(unsigned)((N + tb - 1) / tb), tb, 0, s>>>(N, g->pos.get(), g->nrm.get(), g->w.get(),
-                                                             kap.get(), g->comp.get(), g->centre.get(),
-                                                             g->ctr32hi.get(), g->src.get(), g->selfc.get(),
-                                                             g->src32.get());
+                                                             kap.get(), g->src.get(), g->selfc.get(),
+                                                             g->f32_src.get(), g->f32_lo.get(),
+                                                             g->df_pos.get(), g->df_a.get());
     STOKES_LAUNCHED();
     STOKES_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
   } catch (...) {

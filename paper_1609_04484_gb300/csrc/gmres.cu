@@ -20,7 +20,7 @@ namespace stokes {
 namespace {
 
 constexpr int kChunk = 2048;  // vector elements per CTA in the reductions
-constexpr int kMaxRestart = 200;
+constexpr int kMaxRestart = 1000;
 
 // partial[b * ldp + k] = sum_{i in chunk b} V[k][i] w[i], k < ncols
 __global__ void __launch_bounds__(256)
@@ -228,6 +228,12 @@ void apply_operator(Geom& g, const double* sigma, double* y, int precision, cons
     case STOKES_FP64:
       dlp_apply_f64(g, (const double2*)sigma, (double2*)y, true, g.pos.get(), g.N, done);
       break;
+    case STOKES_FP32:
+      dlp_apply_f32(g, (const double2*)sigma, (double2*)y, true, g.pos.get(), g.N, done);
+      break;
+    case STOKES_DF64:
+      dlp_apply_df64(g, (const double2*)sigma, (double2*)y, true, g.pos.get(), g.N, done);
+      break;
     default:
       throw Error(STOKES_EINVAL, "precision not supported by this operator");
   }
@@ -246,9 +252,9 @@ static double device_norm(Geom& g, const double* v, int64_t n) {
   return h;
 }
 
-SolveResult gmres_solve(Geom& g, const double* f, double* x, double tol, int restart, int max_iter,
-                        int precision, int side) {
-  require(restart >= 1 && restart <= kMaxRestart, "restart must be in [1, 200]");
+static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, int restart, int max_iter,
+                              int precision, int side) {
+  require(restart >= 1 && restart <= kMaxRestart, "restart must be in [1, 1000]");
   require(max_iter >= 1, "max_iter must be >= 1");
   require(tol > 0 && std::isfinite(tol), "tol must be > 0");
   const bool use_pc = g.bd.ready;
@@ -337,7 +343,9 @@ SolveResult gmres_solve(Geom& g, const double* f, double* x, double tol, int res
     k_cycle_start<<<1, 256, 0, s>>>(k.g.get(), m, k.scal.get(), 2, state);
     STOKES_LAUNCHED();
     const int mc = std::min(m, max_iter - iters);
+    std::vector<size_t> iter_first(mc + 1, g.prof.entries.size());
     for (int j = 0; j < mc; ++j) {
+      iter_first[j] = g.prof.entries.size();
       double* vj = k.V.get() + (int64_t)j * n;
       double* vnext = k.V.get() + (int64_t)(j + 1) * n;  // k.w normalised into it
       if (!use_pc) {
@@ -349,6 +357,7 @@ SolveResult gmres_solve(Geom& g, const double* f, double* x, double tol, int res
         apply_operator(g, vj, k.t.get(), precision, state);
         bd_apply(g, k.t.get(), k.w.get(), state);
       }
+      const int pa = g.prof.begin(kProfArnoldi, 8.0 * n * (4.0 * (j + 1) + 4.0), s);
       for (int pass = 0; pass < 2; ++pass) {
         k_dot_partial<<<nblk, 256, 0, s>>>(k.V.get(), n, j + 1, k.w.get(), n, k.partial.get(), ldp, state);
         k_orth_update<<<nblk, 256, 0, s>>>(k.V.get(), n, j + 1, k.partial.get(), ldp, nblk, k.w.get(), n,
@@ -358,8 +367,10 @@ SolveResult gmres_solve(Geom& g, const double* f, double* x, double tol, int res
       k_arnoldi_finish<<<1, 32, 0, s>>>(j, m, np2.get(), nblk, k.H.get(), k.cs.get(), k.sn.get(), k.g.get(),
                                         k.scal.get(), state, rhsnorm, tol);
       k_scale<<<gv, 256, 0, s>>>(k.w.get(), k.scal.get(), 0, vnext, n, state);
+      g.prof.end(pa, s);
       STOKES_LAUNCHED();
     }
+    iter_first[mc] = g.prof.entries.size();
     int hstate[3] = {0, 0, 0};
     STOKES_CUDA(cudaMemcpyAsync(hstate, state, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
     k_lsq_solve<<<1, 32, 0, s>>>(k.H.get(), m, k.g.get(), state, k.y.get());
@@ -372,6 +383,8 @@ SolveResult gmres_solve(Geom& g, const double* f, double* x, double tol, int res
     }
     STOKES_LAUNCHED();
     STOKES_CUDA(cudaStreamSynchronize(s));
+    // launches of iterations after convergence returned at once: not timed work
+    for (size_t e = iter_first[hstate[1]]; e < iter_first[mc]; ++e) g.prof.entries[e].valid = false;
     iters += hstate[1];
     x_is_zero = false;
     if (hstate[2]) {
@@ -385,6 +398,71 @@ SolveResult gmres_solve(Geom& g, const double* f, double* x, double tol, int res
       return res;
     }
   }
+}
+
+}  // namespace stokes
+
+namespace stokes {
+
+// Mixed-precision iterative refinement: the outer residual r = f - A x uses
+// the double-float operator (FP64-class); each correction solves A d = r
+// with GMRES on the FP32 operator to a relative tolerance of 1e-5 (Arnoldi,
+// Givens and least squares stay FP64), then x += d.
+static SolveResult ir_solve(Geom& g, const double* f, double* x, double tol, int restart, int max_iter, int side) {
+  cudaStream_t s = g.stream;
+  const int64_t n = 2 * g.N;
+  DevBuf<double> r, d, t;
+  r.alloc(n);
+  d.alloc(n);
+  t.alloc(n);
+  SolveResult res;
+  const double fnorm = device_norm(g, f, n);
+  if (fnorm == 0.0) {
+    STOKES_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+    STOKES_CUDA(cudaStreamSynchronize(s));
+    return res;
+  }
+  const unsigned gv = grid_for(n);
+  int iters = 0;
+  for (int outer = 0;; ++outer) {
+    apply_operator(g, x, t.get(), STOKES_DF64, nullptr);
+    const int nblk = (int)((n + kChunk - 1) / kChunk);
+    k_residual_norm<<<nblk, 256, 0, s>>>(f, t.get(), r.get(), n, g.kr.partial.get());
+    k_norm_final<<<1, 32, 0, s>>>(g.kr.partial.get(), nblk, g.kr.scal.get(), 2);
+    STOKES_LAUNCHED();
+    double rn = 0.0;
+    STOKES_CUDA(cudaMemcpyAsync(&rn, g.kr.scal.get() + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    STOKES_CUDA(cudaStreamSynchronize(s));
+    res.relres = rn / fnorm;
+    res.pc_relres = res.relres;
+    res.iters = iters;
+    if (!std::isfinite(res.relres)) {
+      res.status = STOKES_EBREAKDOWN;
+      return res;
+    }
+    if (res.relres <= tol) return res;
+    if (iters >= max_iter || outer >= 30) {
+      res.status = STOKES_ENOTCONV;
+      return res;
+    }
+    STOKES_CUDA(cudaMemsetAsync(d.get(), 0, n * sizeof(double), s));
+    const double inner_tol = std::max(1e-5, 0.5 * tol / res.relres);
+    SolveResult in = gmres_core(g, r.get(), d.get(), inner_tol, restart, max_iter - iters, STOKES_FP32, side);
+    iters += in.iters;
+    if (in.status == STOKES_EBREAKDOWN) {
+      res.status = in.status;
+      res.iters = iters;
+      return res;
+    }
+    k_axpy<<<gv, 256, 0, s>>>(x, d.get(), n);
+    STOKES_LAUNCHED();
+  }
+}
+
+SolveResult gmres_solve(Geom& g, const double* f, double* x, double tol, int restart, int max_iter, int precision,
+                        int side) {
+  if (precision == STOKES_MIXED_IR) return ir_solve(g, f, x, tol, restart, max_iter, side);
+  return gmres_core(g, f, x, tol, restart, max_iter, precision, side);
 }
 
 }  // namespace stokes

@@ -92,6 +92,50 @@ struct Krylov {
   int nblk = 0;
 };
 
+// Kernel timing: launches of each kernel class bracketed by CUDA events on
+// the handle's stream while enabled; read back (synchronising) on demand.
+enum ProfKind {
+  kProfPairsF64 = 0, kProfPairsF32 = 1, kProfPairsDF64 = 2, kProfEpilogue = 3,
+  kProfBdApply = 4, kProfArnoldi = 5, kProfBdSetup = 6, kProfKinds = 7
+};
+struct ProfEntry {
+  cudaEvent_t a, b;
+  int kind;
+  double units;
+  bool valid;
+};
+struct Prof {
+  bool on = false;
+  std::vector<ProfEntry> entries;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
+  cudaEvent_t take() {
+    if (pool_used == pool.size()) {
+      cudaEvent_t e;
+      STOKES_CUDA(cudaEventCreate(&e));
+      pool.push_back(e);
+    }
+    return pool[pool_used++];
+  }
+  int begin(int kind, double units, cudaStream_t s) {
+    if (!on) return -1;
+    ProfEntry e{take(), take(), kind, units, true};
+    STOKES_CUDA(cudaEventRecord(e.a, s));
+    entries.push_back(e);
+    return (int)entries.size() - 1;
+  }
+  void end(int idx, cudaStream_t s) {
+    if (idx >= 0) STOKES_CUDA(cudaEventRecord(entries[idx].b, s));
+  }
+  void clear() {
+    entries.clear();
+    pool_used = 0;
+  }
+  ~Prof() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
 struct Geom {
   int64_t N = 0;
   int n_comp = 0;
@@ -112,9 +156,12 @@ struct Geom {
   DevBuf<double2> centre; // completion centre per component
   DevBuf<int> pore_ids;   // the M pore components
 
-  // FP32 node data (coordinates relative to the component centre)
-  DevBuf<float4> src32;   // lx, ly, a_x, a_y
-  DevBuf<float2> ctr32hi, ctr32lo;  // component centre split into float hi + lo
+  // Float copies for the FP32 and double-float kernels: every double v is
+  // split into hi = fl32(v) and lo = fl32(v - hi).
+  DevBuf<float4> f32_src;   // x_hi, y_hi, (w n_x / pi)_hi, (w n_y / pi)_hi
+  DevBuf<float2> f32_lo;    // x_lo, y_lo
+  DevBuf<float4> df_pos;    // x_hi, y_hi, x_lo, y_lo
+  DevBuf<float4> df_a;      // a_x hi, a_y hi, a_x lo, a_y lo  (a = w n / pi)
 
   // workspaces
   DevBuf<double4_32a> mom;    // lambda_x, lambda_y, xi, s0 per component
@@ -124,6 +171,7 @@ struct Geom {
 
   BlockDiag bd;
   Krylov kr;
+  Prof prof;
 };
 
 // ---- geometry.cu ----
@@ -134,6 +182,12 @@ void moments_f64(Geom& g, const double2* sigma, const int* done);
 // interior velocity at T targets (boundary=false). All pointers device.
 void dlp_apply_f64(Geom& g, const double2* sigma, double2* y, bool boundary,
                    const double2* targets, int64_t T, const int* done);
+
+// ---- dlp_f32.cu / dlp_df64.cu ----
+void dlp_apply_f32(Geom& g, const double2* sigma, double2* y, bool boundary,
+                   const double2* targets, int64_t T, const int* done);
+void dlp_apply_df64(Geom& g, const double2* sigma, double2* y, bool boundary,
+                    const double2* targets, int64_t T, const int* done);
 
 // ---- bd.cu ----
 void bd_setup(Geom& g);

@@ -205,3 +205,100 @@ def test_full_size_matvec_sampled_rows(S, dev, rows):
         S.stokes_matvec(G.handle, torch.tensor(sig, device=dev), y, S.STOKES_FP64)
         got = y.cpu().numpy().reshape(-1, 2)[idx]
         assert rel(got, ref) < 1e-12
+
+
+def test_block_diagonal_large_wall_block_triangular_path(S, dev):
+    """A wall block above the explicit-inverse limit (2 x 2200 rows) is
+    applied by blocked triangular solves; it must match the oracle too."""
+    pores = [si.circle_curve((-1.5, 0.1), 0.15, 64), si.circle_curve((1.0, -0.2), 0.2, 64)]
+    g = si.assemble_geometry(pores, si.superellipse_curve(4.0, 1.0, 2200), (4.0, 1.0, 8))
+    v = np.random.default_rng(6).standard_normal(2 * g.n_nodes)
+    ref = O.BlockDiagonal(g).apply(v)
+    with S.Geometry(g) as G:
+        S.stokes_precond_setup(G.handle, S.STOKES_PC_BLOCKDIAG)
+        z = np.empty_like(v)
+        S.stokes_precond_apply(G.handle, v, z)
+        assert rel(z, ref) < 1e-11
+
+
+def test_full_size_block_diagonal_sampled_rows(S, dev):
+    """136,192-node geometry: for sampled rows i of each sampled block k,
+    (A_kk z_k)_i equals v_i, with A_kk's rows from the oracle."""
+    g = si.cached_geometry("cfg2", 0)
+    v = np.random.default_rng(7).standard_normal(2 * g.n_nodes)
+    with S.Geometry(g) as G:
+        S.stokes_precond_setup(G.handle, S.STOKES_PC_BLOCKDIAG)
+        z = np.empty_like(v)
+        S.stokes_precond_apply(G.handle, v, z)
+    rng = np.random.default_rng(8)
+    for k in [0, 517, g.n_pores - 1, g.outer_comp]:
+        sl = g.comp_slice(k)
+        cols = np.arange(sl.start, sl.stop)
+        rows = np.sort(rng.choice(cols, 16, replace=False))
+        B = O.operator_blocks(g, rows, cols)           # (16, n_k, 2, 2)
+        Az = np.einsum("rcab,cb->ra", B, z.reshape(-1, 2)[cols])
+        want = v.reshape(-1, 2)[rows]
+        assert np.abs(Az - want).max() < 1e-9 * np.abs(want).max(), k
+
+
+@pytest.mark.parametrize("prec,bound", [("DF64", 1e-12), ("FP32", 2e-6)])
+def test_matvec_reduced_precision_matches_oracle(S, dev, case, prec, bound):
+    """DF64 (double-float pair sums) meets the FP64 bound; FP32 is bounded
+    by single-precision rounding of ~N-term sums (2e-6 relative)."""
+    name, g = case
+    sig = si.random_density(g, 4).reshape(-1)
+    ref = O.matvec(g, sig)
+    with S.Geometry(g) as G:
+        y = np.empty_like(sig)
+        S.stokes_matvec(G.handle, sig, y, getattr(S, "STOKES_" + prec))
+        assert rel(y, ref) < bound
+
+
+@pytest.mark.parametrize("prec,bound", [("DF64", 1e-12), ("FP32", 2e-6)])
+def test_velocity_reduced_precision(S, dev, prec, bound):
+    g = si.cached_geometry("cfg1", 0)
+    sig = si.random_density(g, 5).reshape(-1)
+    T = si.interior_targets(g, 1000, min_dist=0.05, seed=12)
+    ref = O.velocity(g, sig, T)
+    with S.Geometry(g) as G:
+        u = np.empty(T.size)
+        S.stokes_eval_velocity(G.handle, sig, T.reshape(-1), u, getattr(S, "STOKES_" + prec))
+        assert rel(u, ref) < bound
+
+
+@pytest.mark.parametrize("prec", ["DF64", "MIXED_IR"])
+def test_gmres_reduced_precision_solves_to_fp64_accuracy(S, dev, prec):
+    """DF64 GMRES and mixed-precision refinement reach a true (FP64-class)
+    relative residual of 1e-12 and the dense FP64 solution."""
+    g = si.cached_geometry("cfg1", 0)
+    f = si.pipe_bc(g).reshape(-1)
+    ref = O.solve_dense(g, f)
+    with S.Geometry(g) as G:
+        S.stokes_precond_setup(G.handle)
+        sig = np.zeros_like(f)
+        code, iters, rr, _ = S.stokes_gmres_solve(G.handle, f, sig, tol=1e-12, restart=50,
+                                                  precision=getattr(S, "STOKES_" + prec))
+        assert code == S.STOKES_OK and rr <= 1e-12
+        assert rel(sig, ref) < 1e-10
+        # and the oracle agrees that the residual is small
+        assert np.linalg.norm(f - O.matvec(g, sig)) / np.linalg.norm(f) < 1e-11
+
+
+def test_profile_records_pair_launches(S, dev):
+    g = si.cached_geometry("cfg1", 0)
+    f = si.pipe_bc(g).reshape(-1)
+    with S.Geometry(g) as G:
+        S.stokes_precond_setup(G.handle)
+        S.stokes_profile_enable(G.handle, True)
+        sig = np.zeros_like(f)
+        code, iters, rr, _ = S.stokes_gmres_solve(G.handle, f, sig, tol=1e-10, restart=30, precision=S.STOKES_DF64)
+        n, ms, units = S.stokes_profile_read(G.handle, S.STOKES_PROF_PAIRS_DF64)
+        cycles = -(-iters // 30)
+        # one pair launch per iteration plus one residual per restart after the first
+        assert n == iters + cycles - 1
+        assert units == pytest.approx(n * g.n_nodes**2)
+        assert ms > 0
+        nb, msb, ub = S.stokes_profile_read(G.handle, S.STOKES_PROF_BD_APPLY)
+        assert nb == iters + cycles and msb > 0
+        S.stokes_profile_enable(G.handle, False)
+        assert S.stokes_profile_read(G.handle, S.STOKES_PROF_PAIRS_DF64)[0] == 0
