@@ -189,6 +189,12 @@ int stokes_profile_enable(stokes_geom* g, int on);
 int stokes_profile_read(stokes_geom* g, int kind, int64_t* launches, double* total_ms,
                         double* total_units);
 
+/* Number of library kernels that have started on the current device since
+ * the library was loaded (each kernel counts itself once when it begins;
+ * kernels that return early because a solve already converged count too).
+ * Synchronises the device; -1 on error. */
+int64_t stokes_kernel_launches(void);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* stokes_last_error(void);
 

@@ -23,7 +23,7 @@ __all__ = [
     "stokes_gmres_solve", "stokes_eval_velocity", "stokes_last_error", "Geometry",
     "stokes_profile_enable", "stokes_profile_read", "STOKES_PROF_PAIRS_FP64", "STOKES_PROF_PAIRS_FP32",
     "STOKES_PROF_PAIRS_DF64", "STOKES_PROF_EPILOGUE", "STOKES_PROF_BD_APPLY", "STOKES_PROF_ARNOLDI",
-    "STOKES_PROF_BD_SETUP",
+    "STOKES_PROF_BD_SETUP", "stokes_kernel_launches",
 ]
 
 STOKES_OK, STOKES_EINVAL, STOKES_ENOMEM, STOKES_ECUDA = 0, -1, -2, -3
@@ -61,6 +61,7 @@ def _load():
         "stokes_eval_velocity": (I, [P, P, P, I64, P, I]),
         "stokes_last_error": (ctypes.c_char_p, []),
         "stokes_profile_enable": (I, [P, I]),
+        "stokes_kernel_launches": (I64, []),
         "stokes_profile_read": (I, [P, I, ctypes.POINTER(I64), ctypes.POINTER(D), ctypes.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
@@ -160,6 +161,10 @@ def stokes_eval_velocity(handle, sigma, targets, u, precision=STOKES_FP64):
     T = (targets.numel() if hasattr(targets, "numel") else targets.size) // 2
     _check(lib.stokes_eval_velocity(ctypes.c_void_p(handle), _ptr(sigma, count=n2), _ptr(targets, count=2 * T),
                                     ctypes.c_int64(T), _ptr(u, count=2 * T), int(precision)))
+
+
+def stokes_kernel_launches() -> int:
+    return int(lib.stokes_kernel_launches())
 
 
 def stokes_profile_enable(handle, on=True):

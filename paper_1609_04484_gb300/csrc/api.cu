@@ -230,6 +230,15 @@ int stokes_profile_read(stokes_geom* h, int kind, int64_t* launches, double* tot
   });
 }
 
+int64_t stokes_kernel_launches(void) {
+  try {
+    return (int64_t)(stokes::launches_geometry() + stokes::launches_dlp_f64() + stokes::launches_dlp_f32() +
+                     stokes::launches_dlp_df64() + stokes::launches_bd() + stokes::launches_gmres());
+  } catch (...) {
+    return -1;
+  }
+}
+
 const char* stokes_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"

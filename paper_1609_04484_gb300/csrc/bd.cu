@@ -45,6 +45,7 @@ struct AsmArgs {
 };
 
 __global__ void k_bd_assemble(int64_t total, AsmArgs a) {
+  count_launch();
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     int lo = 0, hi = a.n_comp - 1;  // block containing idx
@@ -135,6 +136,7 @@ k_lu_inv_small(const int* __restrict__ ids, const int64_t* __restrict__ rows,
                const int64_t* __restrict__ elem_off, const int64_t* __restrict__ piv_off,
                double* __restrict__ lu, double* __restrict__ inv, int* __restrict__ piv,
                int* __restrict__ status) {
+  count_launch();
   const int k = ids[blockIdx.x];
   const int64_t m = rows[k];
   double* A = lu + elem_off[k];
@@ -222,6 +224,7 @@ k_lu_inv_small(const int* __restrict__ ids, const int64_t* __restrict__ rows,
 // Per-CTA argmax of |A[r][c]|, r in [c, m).
 __global__ void k_piv_partial(const double* __restrict__ A, int64_t m, int64_t c,
                               double* __restrict__ pv, int64_t* __restrict__ pi) {
+  count_launch();
   double best = -1.0;
   int64_t bi = INT64_MAX;
   for (int64_t r = c + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m;
@@ -241,6 +244,7 @@ __global__ void k_piv_partial(const double* __restrict__ A, int64_t m, int64_t c
 __global__ void k_piv_swap(double* __restrict__ A, int64_t m, int64_t c, int nparts,
                            const double* __restrict__ pv, const int64_t* __restrict__ pi,
                            int* __restrict__ piv, int* __restrict__ status, double* __restrict__ inv_out) {
+  count_launch();
   __shared__ int64_t s_p;
   if (threadIdx.x == 0) {
     double best = -1.0, d = 0.0;
@@ -267,6 +271,7 @@ __global__ void k_piv_swap(double* __restrict__ A, int64_t m, int64_t c, int npa
 // Scale column c below the diagonal and update the panel columns (c, pend).
 __global__ void k_panel_update(double* __restrict__ A, int64_t m, int64_t c, int64_t pend,
                                const double* __restrict__ inv_ptr) {
+  count_launch();
   const double iv = *inv_ptr;
   for (int64_t r = c + 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m;
        r += (int64_t)gridDim.x * blockDim.x) {
@@ -278,6 +283,7 @@ __global__ void k_panel_update(double* __restrict__ A, int64_t m, int64_t c, int
 
 // U12 = L11^-1 A12 for columns [k0 + kb, m): one thread per column.
 __global__ void k_trsm_row_panel(double* __restrict__ A, int64_t m, int64_t k0, int kb) {
+  count_launch();
   const int64_t q = k0 + kb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (q >= m) return;
   double* col = A + q * m + k0;
@@ -302,6 +308,7 @@ __global__ void k_trsm_row_panel(double* __restrict__ A, int64_t m, int64_t k0, 
 // 16 columns of L / rows of U at a time.
 __global__ void __launch_bounds__(256)
 k_gemm_trailing(double* __restrict__ A, int64_t m, int64_t k0, int kb) {
+  count_launch();
   constexpr int kK = 16;
   __shared__ double sL[kK][64 + 1];  // [c][r]
   __shared__ double sU[kK][64 + 1];  // [c][q]
@@ -348,6 +355,7 @@ constexpr int kInvCols = 32;
 __global__ void __launch_bounds__(256)
 k_inv_from_lu(const double* __restrict__ A, int64_t m, const int* __restrict__ perm,
               double* __restrict__ X) {
+  count_launch();
   const int64_t q0 = blockIdx.x * (int64_t)kInvCols;
   const int nq = (int)imin64(kInvCols, m - q0);
   // X[:, q] = P e_q: row r holds 1 where perm[r] == q
@@ -388,6 +396,7 @@ k_bd_gemv(const int* __restrict__ ids, const int64_t* __restrict__ rows,
           const int64_t* __restrict__ elem_off, const int64_t* __restrict__ node_off,
           const double* __restrict__ X, const double* __restrict__ v, double* __restrict__ z,
           const int* __restrict__ done) {
+  count_launch();
   if (done && *done) return;
   const int k = ids[blockIdx.x];
   const int64_t m = rows[k];
@@ -412,6 +421,7 @@ k_bd_gemv(const int* __restrict__ ids, const int64_t* __restrict__ rows,
 // Blocked triangular solves for the largest blocks.
 __global__ void k_permute(const double* __restrict__ v, const int* __restrict__ perm, int64_t m,
                           double* __restrict__ z, const int* __restrict__ done) {
+  count_launch();
   if (done && *done) return;
   const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r < m) z[r] = v[perm[r]];
@@ -422,6 +432,7 @@ __global__ void k_permute(const double* __restrict__ v, const int* __restrict__ 
 __global__ void __launch_bounds__(kTs)
 k_trsv_tile(const double* __restrict__ A, int64_t m, int64_t t0, int lower, double* __restrict__ z,
             const int* __restrict__ done) {
+  count_launch();
   if (done && *done) return;
   extern __shared__ double sT[];  // [kTs][kTs] column-major
   __shared__ double sz[kTs];
@@ -452,6 +463,7 @@ k_trsv_tile(const double* __restrict__ A, int64_t m, int64_t t0, int lower, doub
 // z[r] -= sum_{c in tile} A[r][c] z[c] for rows r in [r_lo, r_hi).
 __global__ void k_trsv_update(const double* __restrict__ A, int64_t m, int64_t t0, int nt, int64_t r_lo,
                               int64_t r_hi, double* __restrict__ z, const int* __restrict__ done) {
+  count_launch();
   if (done && *done) return;
   __shared__ double sz[kTs];
   if (threadIdx.x < nt) sz[threadIdx.x] = z[t0 + threadIdx.x];
@@ -634,4 +646,8 @@ void bd_apply(Geom& g, const double* v, double* z, const int* done) {
   g.prof.end(pb, s);
 }
 
+}  // namespace stokes
+
+namespace stokes {
+unsigned long long launches_bd() { return tu_launches(); }
 }  // namespace stokes

@@ -97,6 +97,7 @@ k_epilogue(int64_t T, int S, const double2* __restrict__ part, int boundary, con
            int outer, const double2* __restrict__ nrm, int M, const int* __restrict__ pore_ids,
            const double2* __restrict__ centre, const double4_32a* __restrict__ mom, double2* __restrict__ y,
            const int* __restrict__ done) {
+  count_launch();
   if (done && *done) return;
   __shared__ double2 s_c[kEpiPores];
   __shared__ double4_32a s_m[kEpiPores];

@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(kThreads)
 k_dlp_pairs_df64(int64_t N, const float4* __restrict__ pos, const float4* __restrict__ aw,
                  const double2* __restrict__ sig, int64_t T, const double2* __restrict__ tgt, int64_t chunk,
                  int self_skip, double2* __restrict__ part, const int* __restrict__ done) {
+  count_launch();
   if (done && *done) return;
   __shared__ float4 s_p[kTile];  // x_hi, y_hi, x_lo, y_lo
   __shared__ float4 s_a[kTile];  // a_x hi, a_y hi, a_x lo, a_y lo
@@ -123,4 +124,8 @@ void dlp_apply_df64(Geom& g, const double2* sigma, double2* y, bool boundary, co
   g.prof.end(pq, g.stream);
 }
 
+}  // namespace stokes
+
+namespace stokes {
+unsigned long long launches_dlp_df64() { return tu_launches(); }
 }  // namespace stokes

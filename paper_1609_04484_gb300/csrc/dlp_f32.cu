@@ -24,6 +24,7 @@ __global__ void __launch_bounds__(kThreads)
 k_dlp_pairs_f32(int64_t N, const float4* __restrict__ src, const float2* __restrict__ lo,
                 const double2* __restrict__ sig, int64_t T, const double2* __restrict__ tgt, int64_t chunk,
                 int self_skip, double2* __restrict__ part, const int* __restrict__ done) {
+  count_launch();
   if (done && *done) return;
   __shared__ float4 s_a[kTile];  // x_hi, y_hi, a_x, a_y
   __shared__ float4 s_b[kTile];  // x_lo, y_lo, sigma_x, sigma_y
@@ -95,4 +96,8 @@ void dlp_apply_f32(Geom& g, const double2* sigma, double2* y, bool boundary, con
   g.prof.end(pq, g.stream);
 }
 
+}  // namespace stokes
+
+namespace stokes {
+unsigned long long launches_dlp_f32() { return tu_launches(); }
 }  // namespace stokes

@@ -18,6 +18,7 @@ __global__ void __launch_bounds__(128)
 k_dlp_pairs_f64(int64_t N, const double4_32a* __restrict__ src, const double2* __restrict__ sig,
                 int64_t T, const double2* __restrict__ tgt, int64_t chunk, int self_skip,
                 double2* __restrict__ part, const int* __restrict__ done) {
+  count_launch();
   if (done && *done) return;
   __shared__ double4_32a s_src[kTile];
   __shared__ double2 s_sig[kTile];
@@ -81,4 +82,8 @@ void dlp_apply_f64(Geom& g, const double2* sigma, double2* y, bool boundary, con
   g.prof.end(pq, g.stream);
 }
 
+}  // namespace stokes
+
+namespace stokes {
+unsigned long long launches_dlp_f64() { return tu_launches(); }
 }  // namespace stokes

@@ -43,6 +43,7 @@ __global__ void k_moments_f64(const double2* __restrict__ pos, const double2* __
                               const double* __restrict__ w, const int64_t* __restrict__ off,
                               const double2* __restrict__ centre, const double2* __restrict__ sig,
                               double4_32a* __restrict__ mom, const int* __restrict__ done) {
+  count_launch();
   if (done && *done) return;
   const int k = blockIdx.x;
   const int64_t a = off[k], b = off[k + 1];
@@ -74,6 +75,7 @@ __global__ void k_prep_nodes(int64_t N, const double2* __restrict__ pos, const d
                              double4_32a* __restrict__ src, double4_32a* __restrict__ selfc,
                              float4* __restrict__ f32_src, float2* __restrict__ f32_lo,
                              float4* __restrict__ df_pos, float4* __restrict__ df_a) {
+  count_launch();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   const double2 p = pos[i], n = nrm[i];
@@ -216,4 +218,8 @@ Geom* geometry_create(const double* nodes, const double* normals, const double* 
   return g;
 }
 
+}  // namespace stokes
+
+namespace stokes {
+unsigned long long launches_geometry() { return tu_launches(); }
 }  // namespace stokes

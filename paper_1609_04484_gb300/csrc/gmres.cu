@@ -26,6 +26,7 @@ constexpr int kMaxRestart = 1000;
 __global__ void __launch_bounds__(256)
 k_dot_partial(const double* __restrict__ V, int64_t ldv, int ncols, const double* __restrict__ w, int64_t n,
               double* __restrict__ partial, int ldp, const int* __restrict__ done) {
+  count_launch();
   if (done && *done) return;
   __shared__ double sw[kChunk];
   const int64_t i0 = blockIdx.x * (int64_t)kChunk;
@@ -49,6 +50,7 @@ __global__ void __launch_bounds__(256)
 k_orth_update(const double* __restrict__ V, int64_t ldv, int ncols, const double* __restrict__ partial, int ldp,
               int nblk, double* __restrict__ w, int64_t n, double* __restrict__ hcol, int accumulate,
               double* __restrict__ normpart, const int* __restrict__ done) {
+  count_launch();
   if (done && *done) return;
   __shared__ double sh[kMaxRestart + 1];
   __shared__ double sred[32];
@@ -87,6 +89,7 @@ k_orth_update(const double* __restrict__ V, int64_t ldv, int ncols, const double
 __global__ void __launch_bounds__(256)
 k_residual_norm(const double* __restrict__ f, const double* __restrict__ t, double* __restrict__ r, int64_t n,
                 double* __restrict__ normpart) {
+  count_launch();
   __shared__ double sred[32];
   const int64_t i0 = blockIdx.x * (int64_t)kChunk;
   const int cn = (int)imin64(kChunk, n - i0);
@@ -111,6 +114,7 @@ k_residual_norm(const double* __restrict__ f, const double* __restrict__ t, doub
 
 // scal[slot] = sqrt(sum normpart), scal[slot + 1] = 1 / that (0 if zero)
 __global__ void k_norm_final(const double* __restrict__ normpart, int nblk, double* __restrict__ scal, int slot) {
+  count_launch();
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int b = 0; b < nblk; ++b) s += normpart[b];
@@ -123,6 +127,7 @@ __global__ void k_norm_final(const double* __restrict__ normpart, int nblk, doub
 // y = x * scal[slot]
 __global__ void k_scale(const double* __restrict__ x, const double* __restrict__ scal, int slot,
                         double* __restrict__ y, int64_t n, const int* __restrict__ done) {
+  count_launch();
   if (done && *done) return;
   const double a = scal[slot];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -132,6 +137,7 @@ __global__ void k_scale(const double* __restrict__ x, const double* __restrict__
 // Start of a cycle: g = (beta, 0, ...), flags cleared.
 __global__ void k_cycle_start(double* __restrict__ g, int m, const double* __restrict__ scal, int slot,
                               int* __restrict__ state) {
+  count_launch();
   for (int i = threadIdx.x; i <= m; i += blockDim.x) g[i] = i == 0 ? scal[slot] : 0.0;
   if (threadIdx.x == 0) {
     state[0] = 0;
@@ -147,6 +153,7 @@ __global__ void k_arnoldi_finish(int j, int m, const double* __restrict__ normpa
                                  double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
                                  double* __restrict__ g, double* __restrict__ scal, int* __restrict__ state,
                                  double rhsnorm, double tol) {
+  count_launch();
   if (state[0]) return;
   if (threadIdx.x != 0) return;
   double s = 0.0;
@@ -185,6 +192,7 @@ __global__ void k_arnoldi_finish(int j, int m, const double* __restrict__ normpa
 // y = R^-1 g over the completed columns (back substitution, one thread).
 __global__ void k_lsq_solve(const double* __restrict__ H, int m, const double* __restrict__ g,
                             const int* __restrict__ state, double* __restrict__ y) {
+  count_launch();
   if (threadIdx.x != 0) return;
   const int jd = state[1];
   for (int i = jd - 1; i >= 0; --i) {
@@ -198,6 +206,7 @@ __global__ void k_lsq_solve(const double* __restrict__ H, int m, const double* _
 // t = sum_{k < jd} y_k V[k]
 __global__ void k_combine(const double* __restrict__ V, int64_t ldv, const double* __restrict__ y,
                           const int* __restrict__ state, double* __restrict__ t, int64_t n) {
+  count_launch();
   __shared__ double sy[kMaxRestart];
   const int jd = state[1];
   for (int k = threadIdx.x; k < jd; k += blockDim.x) sy[k] = y[k];
@@ -210,11 +219,13 @@ __global__ void k_combine(const double* __restrict__ V, int64_t ldv, const doubl
 }
 
 __global__ void k_axpy(double* __restrict__ x, const double* __restrict__ z, int64_t n) {
+  count_launch();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] += z[i];
 }
 
 __global__ void k_copy(double* __restrict__ y, const double* __restrict__ x, int64_t n) {
+  count_launch();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = x[i];
 }
@@ -465,4 +476,8 @@ SolveResult gmres_solve(Geom& g, const double* f, double* x, double tol, int res
   return gmres_core(g, f, x, tol, restart, max_iter, precision, side);
 }
 
+}  // namespace stokes
+
+namespace stokes {
+unsigned long long launches_gmres() { return tu_launches(); }
 }  // namespace stokes

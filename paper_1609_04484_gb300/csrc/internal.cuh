@@ -56,6 +56,18 @@ struct DevBuf {
   T* get() const { return p; }
 };
 
+// Device-side launch counter, one per translation unit: thread 0 of block 0
+// of every kernel adds one when the kernel starts.
+static __device__ unsigned long long g_tu_launches;
+__device__ __forceinline__ void count_launch() {
+  if ((threadIdx.x | threadIdx.y | blockIdx.x | blockIdx.y | blockIdx.z) == 0) atomicAdd(&g_tu_launches, 1ull);
+}
+static inline unsigned long long tu_launches() {
+  unsigned long long v = 0;
+  cudaMemcpyFromSymbol(&v, g_tu_launches, sizeof(v));
+  return v;
+}
+
 __host__ __device__ inline int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
 
 constexpr double kPi = 3.14159265358979323846;
@@ -173,6 +185,14 @@ struct Geom {
   Krylov kr;
   Prof prof;
 };
+
+// per-translation-unit launch counters
+unsigned long long launches_geometry();
+unsigned long long launches_dlp_f64();
+unsigned long long launches_dlp_f32();
+unsigned long long launches_dlp_df64();
+unsigned long long launches_bd();
+unsigned long long launches_gmres();
 
 // ---- geometry.cu ----
 void moments_f64(Geom& g, const double2* sigma, const int* done);

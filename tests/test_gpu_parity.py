@@ -294,8 +294,8 @@ def test_profile_records_pair_launches(S, dev):
         code, iters, rr, _ = S.stokes_gmres_solve(G.handle, f, sig, tol=1e-10, restart=30, precision=S.STOKES_DF64)
         n, ms, units = S.stokes_profile_read(G.handle, S.STOKES_PROF_PAIRS_DF64)
         cycles = -(-iters // 30)
-        # one pair launch per iteration plus one residual per restart after the first
-        assert n == iters + cycles - 1
+        # one pair launch per iteration plus the true residual after each cycle
+        assert n == iters + cycles
         assert units == pytest.approx(n * g.n_nodes**2)
         assert ms > 0
         nb, msb, ub = S.stokes_profile_read(G.handle, S.STOKES_PROF_BD_APPLY)
