@@ -3,9 +3,12 @@
 // On this GPU double precision issues at 1/64 of the single-precision rate,
 // so the pair sum is evaluated with unevaluated sums of two floats
 // (Dekker's double-length arithmetic: TwoSum, FastTwoSum and an FMA-based
-// TwoProduct). Positions, the weighted normals and the density are split
-// hi + lo; r, rho^2, r.a and r.sigma are formed with error-free
-// transformations, 1/rho^2 by one Newton step on a correctly rounded float
+// TwoProduct). Each position is a float on a 2^-8 grid (differences of grid
+// values are exact) plus a float-pair remainder, which keeps ~2^-57 absolute
+// precision, finer than the double input itself; r = (grid difference) +
+// (remainder difference) is then exact to ~2^-48 |r|. The weighted normals
+// and the density are split hi + lo; rho^2, r.a and r.sigma are formed with
+// error-free transformations, 1/rho^2 by one Newton step on a correctly rounded float
 // reciprocal, and the running sum of each tile keeps its rounding errors in
 // a second float (the compensated summation of Ogita, Rump and Oishi).
 // Tile sums are accumulated in double. The diagonal, jump, wall and
@@ -32,18 +35,22 @@ __device__ __forceinline__ void acc_prod(df32& acc, df32 c, df32 r) {
 }
 
 __global__ void __launch_bounds__(kThreads)
-k_dlp_pairs_df64(int64_t N, const float4* __restrict__ pos, const float4* __restrict__ aw,
+k_dlp_pairs_df64(int64_t N, const float2* __restrict__ grid, const float4* __restrict__ pos,
+                 const float4* __restrict__ aw,
                  const double2* __restrict__ sig, int64_t T, const double2* __restrict__ tgt, int64_t chunk,
                  int self_skip, double2* __restrict__ part, const int* __restrict__ done) {
   count_launch();
   if (done && *done) return;
-  __shared__ float4 s_p[kTile];  // x_hi, y_hi, x_lo, y_lo
+  __shared__ float2 s_g[kTile];  // x, y on the 2^-8 grid
+  __shared__ float4 s_p[kTile];  // remainder: x_hi, y_hi, x_lo, y_lo
   __shared__ float4 s_a[kTile];  // a_x hi, a_y hi, a_x lo, a_y lo
   __shared__ float4 s_s[kTile];  // sigma_x hi, sigma_y hi, sigma_x lo, sigma_y lo
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double2 x = make_double2(0.0, 0.0);
   if (i < T) x = tgt[i];
-  const df32 X = dlp::df_from_double(x.x), Y = dlp::df_from_double(x.y);
+  const double gx = rint(x.x * 256.0) * (1.0 / 256.0), gy = rint(x.y * 256.0) * (1.0 / 256.0);
+  const float GX = (float)gx, GY = (float)gy;
+  const df32 X = dlp::df_from_double(x.x - gx), Y = dlp::df_from_double(x.y - gy);
   const int64_t j0 = blockIdx.y * chunk;
   const int64_t j1 = imin64(N, j0 + chunk);
   const int64_t iself = self_skip ? i : -1;
@@ -55,11 +62,13 @@ k_dlp_pairs_df64(int64_t N, const float4* __restrict__ pos, const float4* __rest
       if (j < j1) {
         const double2 sg = sig[j];
         const df32 sx = dlp::df_from_double(sg.x), sy = dlp::df_from_double(sg.y);
+        s_g[q] = grid[j];
         s_p[q] = pos[j];
         s_a[q] = aw[j];
         s_s[q] = make_float4(sx.h, sy.h, sx.l, sy.l);
       } else {
-        s_p[q] = make_float4(1e18f, 1e18f, 0.f, 0.f);
+        s_g[q] = make_float2(1e18f, 1e18f);
+        s_p[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         s_a[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         s_s[q] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
@@ -69,13 +78,19 @@ k_dlp_pairs_df64(int64_t N, const float4* __restrict__ pos, const float4* __rest
     df32 ax = {0.f, 0.f}, ay = {0.f, 0.f};
 #pragma unroll 2
     for (int q = 0; q < kTile; ++q) {
+      const float2 gq = s_g[q];
       const float4 p = s_p[q];
       const float4 a = s_a[q];
       const float4 s = s_s[q];
-      df32 rx = dlp::two_diff(X.h, p.x);
-      rx.l += X.l - p.z;
-      df32 ry = dlp::two_diff(Y.h, p.y);
-      ry.l += Y.l - p.w;
+      // r = (grid difference, exact) + (remainder difference as a float pair)
+      df32 lx = dlp::two_diff(X.h, p.x);
+      lx.l += X.l - p.z;
+      df32 ly = dlp::two_diff(Y.h, p.y);
+      ly.l += Y.l - p.w;
+      df32 rx = dlp::two_sum(GX - gq.x, lx.h);
+      rx.l += lx.l;
+      df32 ry = dlp::two_sum(GY - gq.y, ly.h);
+      ry.l += ly.l;
       // rho^2 = rx^2 + ry^2
       const float px = rx.h * rx.h;
       float ex = fmaf(rx.h, rx.h, -px);
@@ -115,7 +130,8 @@ void dlp_apply_df64(Geom& g, const double2* sigma, double2* y, bool boundary, co
   g.part.alloc((size_t)splits * T);
   dim3 grid((unsigned)((T + kThreads - 1) / kThreads), (unsigned)splits);
   const int pe = g.prof.begin(kProfPairsDF64, (double)g.N * (double)T, g.stream);
-  k_dlp_pairs_df64<<<grid, kThreads, 0, g.stream>>>(g.N, g.df_pos.get(), g.df_a.get(), sigma, T, targets, chunk,
+  k_dlp_pairs_df64<<<grid, kThreads, 0, g.stream>>>(g.N, g.df_grid.get(), g.df_pos.get(), g.df_a.get(), sigma, T,
+                                                     targets, chunk,
                                                      boundary ? 1 : 0, g.part.get(), done);
   STOKES_LAUNCHED();
   g.prof.end(pe, g.stream);

@@ -70,11 +70,15 @@ __device__ __forceinline__ float2 split_f(double v) {
   return make_float2(h, (float)(v - (double)h));
 }
 
+// v = grid + rem: grid is v rounded to a multiple of 2^-8 (exact in float
+// for |v| < 2^15, and so are differences of grid values); |rem| <= 2^-9.
+__device__ __forceinline__ double grid_part(double v) { return rint(v * 256.0) * (1.0 / 256.0); }
+
 __global__ void k_prep_nodes(int64_t N, const double2* __restrict__ pos, const double2* __restrict__ nrm,
                              const double* __restrict__ w, const double* __restrict__ kappa,
                              double4_32a* __restrict__ src, double4_32a* __restrict__ selfc,
                              float4* __restrict__ f32_src, float2* __restrict__ f32_lo,
-                             float4* __restrict__ df_pos, float4* __restrict__ df_a) {
+                             float2* __restrict__ df_grid, float4* __restrict__ df_pos, float4* __restrict__ df_a) {
   count_launch();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -86,7 +90,10 @@ __global__ void k_prep_nodes(int64_t N, const double2* __restrict__ pos, const d
   const float2 sx = split_f(p.x), sy = split_f(p.y), sax = split_f(ax), say = split_f(ay);
   f32_src[i] = make_float4(sx.x, sy.x, sax.x, say.x);
   f32_lo[i] = make_float2(sx.y, sy.y);
-  df_pos[i] = make_float4(sx.x, sy.x, sx.y, sy.y);
+  const double gx = grid_part(p.x), gy = grid_part(p.y);
+  const float2 rx = split_f(p.x - gx), ry = split_f(p.y - gy);
+  df_grid[i] = make_float2((float)gx, (float)gy);
+  df_pos[i] = make_float4(rx.x, ry.x, rx.y, ry.y);
   df_a[i] = make_float4(sax.x, say.x, sax.y, say.y);
 }
 
@@ -128,6 +135,7 @@ Geom* geometry_create(const double* nodes, const double* normals, const double* 
   const int64_t N = offsets[n_comp];
   require(N <= (int64_t)1 << 28, "too many nodes");
 
+
   Geom* g = new Geom();
   try {
     g->N = N;
@@ -150,6 +158,8 @@ Geom* geometry_create(const double* nodes, const double* normals, const double* 
     STOKES_CUDA(cudaStreamSynchronize(s));
     for (int64_t i = 0; i < N; ++i) {
       require(std::isfinite(hx[2 * i]) && std::isfinite(hx[2 * i + 1]), "non-finite node");
+      require(std::fabs(hx[2 * i]) < 16384.0 && std::fabs(hx[2 * i + 1]) < 16384.0,
+              "node coordinates must be below 2^14 in magnitude");
       require(std::isfinite(hw[i]) && hw[i] > 0, "weights must be finite and > 0");
       require(std::isfinite(hk[i]), "non-finite curvature");
       const double nn = std::hypot(hn[2 * i], hn[2 * i + 1]);
@@ -188,6 +198,7 @@ Geom* geometry_create(const double* nodes, const double* normals, const double* 
     g->selfc.alloc(N);
     g->f32_src.alloc(N);
     g->f32_lo.alloc(N);
+    g->df_grid.alloc(N);
     g->df_pos.alloc(N);
     g->df_a.alloc(N);
     g->comp.alloc(N);
@@ -207,7 +218,7 @@ Geom* geometry_create(const double* nodes, const double* normals, const double* 
     const int tb = 256;
     k_prep_nodes<<<(unsigned)((N + tb - 1) / tb), tb, 0, s>>>(N, g->pos.get(), g->nrm.get(), g->w.get(),
                                                              kap.get(), g->src.get(), g->selfc.get(),
-                                                             g->f32_src.get(), g->f32_lo.get(),
+                                                             g->f32_src.get(), g->f32_lo.get(), g->df_grid.get(),
                                                              g->df_pos.get(), g->df_a.get());
     STOKES_LAUNCHED();
     STOKES_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope

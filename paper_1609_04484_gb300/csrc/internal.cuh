@@ -172,7 +172,8 @@ struct Geom {
   // split into hi = fl32(v) and lo = fl32(v - hi).
   DevBuf<float4> f32_src;   // x_hi, y_hi, (w n_x / pi)_hi, (w n_y / pi)_hi
   DevBuf<float2> f32_lo;    // x_lo, y_lo
-  DevBuf<float4> df_pos;    // x_hi, y_hi, x_lo, y_lo
+  DevBuf<float2> df_grid;   // x, y rounded to multiples of 2^-8 (exact differences)
+  DevBuf<float4> df_pos;    // remainder x - grid as a float pair: rx_hi, ry_hi, rx_lo, ry_lo
   DevBuf<float4> df_a;      // a_x hi, a_y hi, a_x lo, a_y lo  (a = w n / pi)
 
   // workspaces
