@@ -250,7 +250,33 @@ void apply_operator(Geom& g, const double* sigma, double* y, int precision, cons
   }
 }
 
-// ||v|| on the device, copied to the host (synchronises).
+// Workspace of the Krylov solver for restart length m (grows on demand).
+static void krylov_alloc(Geom& g, int m) {
+  Krylov& k = g.kr;
+  const int64_t n = 2 * g.N;
+  const int nblk = (int)((n + kChunk - 1) / kChunk);
+  const int ldp = kMaxRestart + 1;
+  if (k.m < m || k.n2 != n) {
+    k.V.alloc((size_t)(m + 1) * n);
+    k.Z.alloc(n);
+    k.w.alloc(n);
+    k.t.alloc(n);
+    k.r.alloc(n);
+    k.H.alloc((size_t)(m + 1) * m);
+    k.cs.alloc(m);
+    k.sn.alloc(m);
+    k.g.alloc(m + 1);
+    k.y.alloc(m);
+    k.m = m;
+    k.n2 = n;
+  }
+  k.partial.alloc((size_t)nblk * ldp + 8);
+  k.scal.alloc(8);
+  k.state.alloc(4);
+  k.nblk = nblk;
+}
+
+// ||v|| on the device, copied to the host (synchronises). Needs krylov_alloc.
 static double device_norm(Geom& g, const double* v, int64_t n) {
   Krylov& k = g.kr;
   const int nblk = (int)((n + kChunk - 1) / kChunk);
@@ -276,25 +302,7 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
   Krylov& k = g.kr;
   const int nblk = (int)((n + kChunk - 1) / kChunk);
   const int ldp = kMaxRestart + 1;
-  if (k.m < m || k.n2 != n) {
-    k.V.alloc((size_t)(m + 1) * n);
-    k.Z.alloc(n);
-    k.w.alloc(n);
-    k.t.alloc(n);
-    k.r.alloc(n);
-    k.partial.alloc((size_t)nblk * ldp + 8);
-    k.H.alloc((size_t)(m + 1) * m);
-    k.cs.alloc(m);
-    k.sn.alloc(m);
-    k.g.alloc(m + 1);
-    k.y.alloc(m);
-    k.scal.alloc(8);
-    k.state.alloc(4);
-    k.m = m;
-    k.n2 = n;
-  }
-  k.nblk = nblk;
-  k.partial.alloc((size_t)nblk * ldp + 8);
+  krylov_alloc(g, m);
   double* normpart = k.partial.get();  // reductions of norms share the partial buffer
   DevBuf<double> np2;                  // separate buffer for the norm partials inside a step
   np2.alloc(nblk);
@@ -426,6 +434,8 @@ static SolveResult ir_solve(Geom& g, const double* f, double* x, double tol, int
   r.alloc(n);
   d.alloc(n);
   t.alloc(n);
+  require(restart >= 1 && restart <= kMaxRestart, "restart must be in [1, 1000]");
+  krylov_alloc(g, restart);  // device_norm and the residual below use its buffers
   SolveResult res;
   const double fnorm = device_norm(g, f, n);
   if (fnorm == 0.0) {
