@@ -139,8 +139,9 @@ int stokes_precond_apply(stokes_geom* g, const double* v, double* z);
  *   precision STOKES_FP64, STOKES_DF64 (operator arithmetic; Arnoldi, Givens
  *             and the least-squares update always FP64) or STOKES_MIXED_IR
  *             (iterative refinement: outer residual with the DF64 operator,
- *             corrections by GMRES on the FP32 operator to relative
- *             tolerance max(1e-5, tol / (2 |r| / |f|)); iters_out counts the
+ *             corrections by GMRES on the FP32 operator until its Arnoldi
+ *             residual estimate is below max(1e-4, tol / (2 |r| / |f|));
+ *             STOKES_TRACE=1 in the environment prints each step; iters_out counts the
  *             inner iterations, both residual outputs are the outer one)
  *   pc_side STOKES_PC_RIGHT (default; stops on the true residual
  *           |f - A sigma| / |f|) or STOKES_PC_LEFT (Sec. 4.1; stops on the
