@@ -134,7 +134,7 @@ int stokes_precond_apply(stokes_geom* g, const double* v, double* z);
  * stokes_precond_setup call (none if never set up).
  *   f       [2N] right-hand side (the boundary data at the nodes)
  *   tol     relative residual tolerance (> 0)
- *   restart Krylov dimension per cycle, 1..1000
+ *   restart Krylov dimension per cycle, 1..8192 (basis of restart+1 vectors of 2N doubles)
  *   max_iter total inner iterations (>= 1)
  *   precision STOKES_FP64, STOKES_DF64 (operator arithmetic; Arnoldi, Givens
  *             and the least-squares update always FP64) or STOKES_MIXED_IR

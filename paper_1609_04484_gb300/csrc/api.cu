@@ -141,6 +141,7 @@ int stokes_precond_apply(stokes_geom* h, const double* v, double* z) {
     stokes::bd_apply(g, vi, zo, nullptr);
     STOKES_LAUNCHED();
     finish_output(g, z, zo, n, staged);
+    stokes::bd_check_barrier(g);
   });
 }
 
@@ -233,7 +234,7 @@ int stokes_profile_read(stokes_geom* h, int kind, int64_t* launches, double* tot
 int64_t stokes_kernel_launches(void) {
   try {
     return (int64_t)(stokes::launches_geometry() + stokes::launches_dlp_f64() + stokes::launches_dlp_f32() +
-                     stokes::launches_dlp_df64() + stokes::launches_bd() + stokes::launches_gmres());
+                     stokes::launches_dlp_df64() + stokes::launches_bd() + stokes::launches_bd_trsv() + stokes::launches_gmres());
   } catch (...) {
     return -1;
   }

@@ -10,9 +10,11 @@
 //   kSmall < m <= kInv blocked right-looking LU (panel of kNb columns, FP64
 //                      tiled GEMM for the trailing update), inverse from the
 //                      factors with many CTAs (one tile of columns each);
-//   m > kInv           blocked LU, applied by blocked triangular solves.
+//   m > kInv           blocked LU, applied by a persistent triangular solve
+//                      (bd_trsv.cu).
 // The apply z = P^-1 v is a batched matrix-vector product with the inverses
-// (memory-bound) plus the triangular solves of the largest blocks.
+// (memory-bound) plus the triangular solves of the largest blocks; the
+// inner solves of the mixed-precision refinement use float copies of both.
 #include <algorithm>
 #include <cmath>
 
@@ -25,7 +27,6 @@ namespace {
 constexpr int64_t kSmall = 512;
 constexpr int64_t kInv = 4096;
 constexpr int kNb = 64;     // panel width of the blocked LU
-constexpr int kTs = 128;    // diagonal tile of the blocked triangular solves
 
 // ---------------------------------------------------------------------------
 // Assembly
@@ -391,10 +392,11 @@ k_inv_from_lu(const double* __restrict__ A, int64_t m, const int* __restrict__ p
 // z_k = X_k v_k for the blocks in `ids`; CTA (b, s) computes rows
 // [64 s, 64 s + 64) of block ids[b]; the 256 threads split the columns in
 // four interleaved phases and combine them in shared memory.
+template <class T>
 __global__ void __launch_bounds__(256)
 k_bd_gemv(const int* __restrict__ ids, const int64_t* __restrict__ rows,
           const int64_t* __restrict__ elem_off, const int64_t* __restrict__ node_off,
-          const double* __restrict__ X, const double* __restrict__ v, double* __restrict__ z,
+          const T* __restrict__ X, const double* __restrict__ v, double* __restrict__ z,
           const int* __restrict__ done) {
   count_launch();
   if (done && *done) return;
@@ -402,77 +404,27 @@ k_bd_gemv(const int* __restrict__ ids, const int64_t* __restrict__ rows,
   const int64_t m = rows[k];
   const int64_t r0 = blockIdx.y * (int64_t)64;
   if (r0 >= m) return;
-  const double* Xk = X + elem_off[k];
+  const T* Xk = X + elem_off[k];
   const double* vk = v + 2 * node_off[k];
-  extern __shared__ double sv[];
-  __shared__ double red[4][64];
-  for (int64_t q = threadIdx.x; q < m; q += blockDim.x) sv[q] = vk[q];
+  extern __shared__ double sv_raw[];
+  T* sv = reinterpret_cast<T*>(sv_raw);
+  __shared__ T red[4][64];
+  for (int64_t q = threadIdx.x; q < m; q += blockDim.x) sv[q] = (T)vk[q];
   __syncthreads();
   const int rr = threadIdx.x & 63, ph = threadIdx.x >> 6;
   const int64_t r = r0 + rr;
-  double acc = 0.0;
+  T acc = 0;
   if (r < m)
-    for (int64_t q = ph; q < m; q += 4) acc = fma(Xk[q * m + r], sv[q], acc);
+    for (int64_t q = ph; q < m; q += 4) acc += Xk[q * m + r] * sv[q];
   red[ph][rr] = acc;
   __syncthreads();
-  if (ph == 0 && r < m) z[2 * node_off[k] + r] = (red[0][rr] + red[1][rr]) + (red[2][rr] + red[3][rr]);
+  if (ph == 0 && r < m) z[2 * node_off[k] + r] = (double)((red[0][rr] + red[1][rr]) + (red[2][rr] + red[3][rr]));
 }
 
-// Blocked triangular solves for the largest blocks.
-__global__ void k_permute(const double* __restrict__ v, const int* __restrict__ perm, int64_t m,
-                          double* __restrict__ z, const int* __restrict__ done) {
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
   count_launch();
-  if (done && *done) return;
-  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (r < m) z[r] = v[perm[r]];
-}
-
-// Solve the kTs x kTs diagonal tile starting at row t0 in place:
-// lower (unit) if lower, else upper (non-unit).
-__global__ void __launch_bounds__(kTs)
-k_trsv_tile(const double* __restrict__ A, int64_t m, int64_t t0, int lower, double* __restrict__ z,
-            const int* __restrict__ done) {
-  count_launch();
-  if (done && *done) return;
-  extern __shared__ double sT[];  // [kTs][kTs] column-major
-  __shared__ double sz[kTs];
-  const int nt = (int)imin64(kTs, m - t0);
-  for (int e = threadIdx.x; e < nt * nt; e += blockDim.x) {
-    const int q = e / nt, r = e % nt;
-    sT[q * kTs + r] = A[(t0 + q) * m + t0 + r];
-  }
-  if (threadIdx.x < nt) sz[threadIdx.x] = z[t0 + threadIdx.x];
-  __syncthreads();
-  const int r = threadIdx.x;
-  if (lower) {
-    for (int c = 0; c < nt; ++c) {
-      if (r > c && r < nt) sz[r] -= sT[c * kTs + r] * sz[c];
-      __syncthreads();
-    }
-  } else {
-    for (int c = nt - 1; c >= 0; --c) {
-      if (r == c) sz[c] /= sT[c * kTs + c];
-      __syncthreads();
-      if (r < c) sz[r] -= sT[c * kTs + r] * sz[c];
-      __syncthreads();
-    }
-  }
-  if (r < nt) z[t0 + r] = sz[r];
-}
-
-// z[r] -= sum_{c in tile} A[r][c] z[c] for rows r in [r_lo, r_hi).
-__global__ void k_trsv_update(const double* __restrict__ A, int64_t m, int64_t t0, int nt, int64_t r_lo,
-                              int64_t r_hi, double* __restrict__ z, const int* __restrict__ done) {
-  count_launch();
-  if (done && *done) return;
-  __shared__ double sz[kTs];
-  if (threadIdx.x < nt) sz[threadIdx.x] = z[t0 + threadIdx.x];
-  __syncthreads();
-  const int64_t r = r_lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (r >= r_hi) return;
-  double acc = 0.0;
-  for (int c = 0; c < nt; ++c) acc = fma(A[(t0 + c) * m + r], sz[c], acc);
-  z[r] -= acc;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
 }
 
 }  // namespace
@@ -480,9 +432,9 @@ __global__ void k_trsv_update(const double* __restrict__ A, int64_t m, int64_t t
 void bd_init_attributes() {
   static bool inited = false;
   if (inited) return;
-  STOKES_CUDA(cudaFuncSetAttribute(k_trsv_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   kTs * kTs * (int)sizeof(double)));
-  STOKES_CUDA(cudaFuncSetAttribute(k_bd_gemv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  STOKES_CUDA(cudaFuncSetAttribute(k_bd_gemv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(kInv * sizeof(double))));
+  STOKES_CUDA(cudaFuncSetAttribute(k_bd_gemv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)(kInv * sizeof(double))));
   inited = true;
 }
@@ -603,45 +555,61 @@ void bd_setup(Geom& g) {
         b.lu.get() + b.elem_off[k], m, b.perm.get() + b.piv_off[k], b.inv.get() + b.elem_off[k]);
     STOKES_LAUNCHED();
   }
+  // single-precision copies: all inverses, and the factors of the blocks
+  // applied by triangular solves
+  b.inv32.alloc(total);
+  k_to_f32<<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32), 256, 0, s>>>(b.inv.get(), b.inv32.get(),
+                                                                                     total);
+  STOKES_LAUNCHED();
+  b.lu32_off.assign(nc, -1);
+  int64_t tri_total = 0, tri_max = 0;
+  for (int k : b.tri_ids) {
+    b.lu32_off[k] = tri_total;
+    tri_total += b.rows[k] * b.rows[k];
+    tri_max = std::max(tri_max, b.rows[k]);
+  }
+  if (tri_total) {
+    b.lu32.alloc(tri_total);
+    b.work32.alloc(tri_max);
+    b.work64.alloc(tri_max);
+    for (int k : b.tri_ids) {
+      const int64_t mm = b.rows[k] * b.rows[k];
+      k_to_f32<<<(unsigned)std::min<int64_t>((mm + 255) / 256, 152 * 32), 256, 0, s>>>(
+          b.lu.get() + b.elem_off[k], b.lu32.get() + b.lu32_off[k], mm);
+      STOKES_LAUNCHED();
+    }
+  }
   g.prof.end(ps, s);
   STOKES_CUDA(cudaStreamSynchronize(s));
   b.ready = true;
 }
 
-void bd_apply(Geom& g, const double* v, double* z, const int* done) {
+void bd_apply(Geom& g, const double* v, double* z, const int* done, bool f32) {
   BlockDiag& b = g.bd;
   require(b.ready, "preconditioner not set up", STOKES_ESTATE);
   cudaStream_t s = g.stream;
   // algorithmic bytes: every block's inverse or factors once, v in, z out
-  const int pb = g.prof.begin(kProfBdApply, 8.0 * (double)b.elem_off[g.n_comp] + 32.0 * (double)g.N, s);
+  const double wbytes = f32 ? 4.0 : 8.0;
+  const int pb = g.prof.begin(kProfBdApply, wbytes * (double)b.elem_off[g.n_comp] + 32.0 * (double)g.N, s);
   if (!b.inv_ids.empty()) {
     dim3 grid((unsigned)b.inv_ids.size(), (unsigned)((b.max_inv_rows + 63) / 64));
-    k_bd_gemv<<<grid, 256, b.max_inv_rows * sizeof(double), s>>>(
-        b.d_inv_ids.get(), b.d_rows.get(), b.d_elem_off.get(), b.d_node_off.get(), b.inv.get(), v, z, done);
+    const size_t sm = b.max_inv_rows * sizeof(double);
+    if (f32)
+      k_bd_gemv<float><<<grid, 256, sm, s>>>(b.d_inv_ids.get(), b.d_rows.get(), b.d_elem_off.get(),
+                                             b.d_node_off.get(), b.inv32.get(), v, z, done);
+    else
+      k_bd_gemv<double><<<grid, 256, sm, s>>>(b.d_inv_ids.get(), b.d_rows.get(), b.d_elem_off.get(),
+                                              b.d_node_off.get(), b.inv.get(), v, z, done);
     STOKES_LAUNCHED();
   }
   for (int k : b.tri_ids) {
     const int64_t m = b.rows[k];
     const int64_t o = 2 * g.off[k];
-    const double* A = b.lu.get() + b.elem_off[k];
-    double* zk = z + o;
-    k_permute<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(v + o, b.perm.get() + b.piv_off[k], m, zk, done);
-    const size_t sm = (size_t)kTs * kTs * sizeof(double);
-    for (int64_t t0 = 0; t0 < m; t0 += kTs) {
-      const int nt = (int)imin64(kTs, m - t0);
-      k_trsv_tile<<<1, kTs, sm, s>>>(A, m, t0, 1, zk, done);
-      const int64_t lo = t0 + nt;
-      if (lo < m)
-        k_trsv_update<<<(unsigned)((m - lo + 255) / 256), 256, 0, s>>>(A, m, t0, nt, lo, m, zk, done);
-    }
-    const int64_t ntile = (m + kTs - 1) / kTs;
-    for (int64_t ti = ntile - 1; ti >= 0; --ti) {
-      const int64_t t0 = ti * kTs;
-      const int nt = (int)imin64(kTs, m - t0);
-      k_trsv_tile<<<1, kTs, sm, s>>>(A, m, t0, 0, zk, done);
-      if (t0 > 0) k_trsv_update<<<(unsigned)((t0 + 255) / 256), 256, 0, s>>>(A, m, t0, nt, 0, t0, zk, done);
-    }
-    STOKES_LAUNCHED();
+    const int* perm = b.perm.get() + b.piv_off[k];
+    if (f32)
+      lu_solve_persistent<float>(g, b.lu32.get() + b.lu32_off[k], m, perm, v + o, z + o, b.work32.get(), done);
+    else
+      lu_solve_persistent<double>(g, b.lu.get() + b.elem_off[k], m, perm, v + o, z + o, b.work64.get(), done);
   }
   g.prof.end(pb, s);
 }

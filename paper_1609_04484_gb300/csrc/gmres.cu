@@ -22,7 +22,7 @@ namespace stokes {
 namespace {
 
 constexpr int kChunk = 2048;  // vector elements per CTA in the reductions
-constexpr int kMaxRestart = 1000;
+constexpr int kMaxRestart = 8192;
 
 // partial[b * ldp + k] = sum_{i in chunk b} V[k][i] w[i], k < ncols
 __global__ void __launch_bounds__(256)
@@ -46,30 +46,35 @@ k_dot_partial(const double* __restrict__ V, int64_t ldv, int ncols, const double
   }
 }
 
-// h_k = sum_b partial[b][k]; w -= sum_k h_k V[k]; optionally H[:, col] (+)= h
-// (block 0) and normpart[b] = sum_{i in chunk b} w_i^2.
-__global__ void __launch_bounds__(256)
-k_orth_update(const double* __restrict__ V, int64_t ldv, int ncols, const double* __restrict__ partial, int ldp,
-              int nblk, double* __restrict__ w, int64_t n, double* __restrict__ hcol, int accumulate,
-              double* __restrict__ normpart, const int* __restrict__ done) {
+// h_k = sum_b partial[b][k] for k < ncols (fixed order), written to hvec and
+// to the Hessenberg column (pass 0: =, pass 1: +=).
+__global__ void k_reduce_partials(const double* __restrict__ partial, int ldp, int nblk, int ncols,
+                                  double* __restrict__ hvec, double* __restrict__ hcol, int accumulate,
+                                  const int* __restrict__ done) {
   count_launch();
   if (done && *done) return;
-  __shared__ double sh[kMaxRestart + 1];
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ncols) return;
+  double h = 0.0;
+  for (int b = 0; b < nblk; ++b) h += partial[(int64_t)b * ldp + k];
+  hvec[k] = h;
+  hcol[k] = accumulate ? hcol[k] + h : h;
+}
+
+// w -= sum_k h_k V[k]; normpart[b] = sum_{i in chunk b} w_i^2 (if given).
+__global__ void __launch_bounds__(256)
+k_orth_update(const double* __restrict__ V, int64_t ldv, int ncols, const double* __restrict__ hvec,
+              double* __restrict__ w, int64_t n, double* __restrict__ normpart, const int* __restrict__ done) {
+  count_launch();
+  if (done && *done) return;
   __shared__ double sred[32];
-  for (int k = threadIdx.x; k < ncols; k += blockDim.x) {
-    double h = 0.0;
-    for (int b = 0; b < nblk; ++b) h += partial[b * ldp + k];
-    sh[k] = h;
-    if (blockIdx.x == 0 && hcol) hcol[k] = accumulate ? hcol[k] + h : h;
-  }
-  __syncthreads();
   const int64_t i0 = blockIdx.x * (int64_t)kChunk;
   const int cn = (int)imin64(kChunk, n - i0);
   double sq = 0.0;
   for (int e = threadIdx.x; e < cn; e += blockDim.x) {
     const int64_t i = i0 + e;
     double acc = w[i];
-    for (int k = 0; k < ncols; ++k) acc = fma(-sh[k], V[k * ldv + i], acc);
+    for (int k = 0; k < ncols; ++k) acc = fma(-hvec[k], V[k * ldv + i], acc);
     w[i] = acc;
     sq = fma(acc, acc, sq);
   }
@@ -191,17 +196,26 @@ __global__ void k_arnoldi_finish(int j, int m, const double* __restrict__ normpa
   }
 }
 
-// y = R^-1 g over the completed columns (back substitution, one thread).
-__global__ void k_lsq_solve(const double* __restrict__ H, int m, const double* __restrict__ g,
-                            const int* __restrict__ state, double* __restrict__ y) {
+// y = R^-1 g over the completed columns: column-oriented back substitution
+// by one CTA (after y_i is known, every thread updates its rows above).
+__global__ void __launch_bounds__(256)
+k_lsq_solve(const double* __restrict__ H, int m, const double* __restrict__ g, const int* __restrict__ state,
+            double* __restrict__ y, double* __restrict__ work) {
   count_launch();
-  if (threadIdx.x != 0) return;
   const int jd = state[1];
+  for (int i = threadIdx.x; i < jd; i += blockDim.x) work[i] = g[i];
+  __syncthreads();
   for (int i = jd - 1; i >= 0; --i) {
-    double acc = g[i];
-    for (int k = i + 1; k < jd; ++k) acc -= H[(int64_t)k * (m + 1) + i] * y[k];
-    const double d = H[(int64_t)i * (m + 1) + i];
-    y[i] = d != 0.0 ? acc / d : 0.0;
+    __shared__ double yi;
+    if (threadIdx.x == 0) {
+      const double d = H[(int64_t)i * (m + 1) + i];
+      yi = d != 0.0 ? work[i] / d : 0.0;
+      y[i] = yi;
+    }
+    __syncthreads();
+    const double v = yi;
+    for (int r = threadIdx.x; r < i; r += blockDim.x) work[r] -= H[(int64_t)i * (m + 1) + r] * v;
+    __syncthreads();
   }
 }
 
@@ -209,13 +223,10 @@ __global__ void k_lsq_solve(const double* __restrict__ H, int m, const double* _
 __global__ void k_combine(const double* __restrict__ V, int64_t ldv, const double* __restrict__ y,
                           const int* __restrict__ state, double* __restrict__ t, int64_t n) {
   count_launch();
-  __shared__ double sy[kMaxRestart];
   const int jd = state[1];
-  for (int k = threadIdx.x; k < jd; k += blockDim.x) sy[k] = y[k];
-  __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double acc = 0.0;
-    for (int k = 0; k < jd; ++k) acc = fma(sy[k], V[k * ldv + i], acc);
+    for (int k = 0; k < jd; ++k) acc = fma(y[k], V[k * ldv + i], acc);
     t[i] = acc;
   }
 }
@@ -257,7 +268,7 @@ static void krylov_alloc(Geom& g, int m) {
   Krylov& k = g.kr;
   const int64_t n = 2 * g.N;
   const int nblk = (int)((n + kChunk - 1) / kChunk);
-  const int ldp = kMaxRestart + 1;
+  const int ldp = std::max(m, k.m) + 1;
   if (k.m < m || k.n2 != n) {
     k.V.alloc((size_t)(m + 1) * n);
     k.Z.alloc(n);
@@ -268,7 +279,7 @@ static void krylov_alloc(Geom& g, int m) {
     k.cs.alloc(m);
     k.sn.alloc(m);
     k.g.alloc(m + 1);
-    k.y.alloc(m);
+    k.y.alloc(2 * (size_t)(m + 1));  // projection coefficients / y, then back-substitution work
     k.m = m;
     k.n2 = n;
   }
@@ -297,7 +308,7 @@ static double device_norm(Geom& g, const double* v, int64_t n) {
 // the inner tolerance.
 static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, int restart, int max_iter,
                               int precision, int side, bool inner = false) {
-  require(restart >= 1 && restart <= kMaxRestart, "restart must be in [1, 1000]");
+  require(restart >= 1 && restart <= kMaxRestart, "restart must be in [1, 8192]");
   require(max_iter >= 1, "max_iter must be >= 1");
   require(tol > 0 && std::isfinite(tol), "tol must be > 0");
   const bool use_pc = g.bd.ready;
@@ -307,7 +318,7 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
   const int m = restart;
   Krylov& k = g.kr;
   const int nblk = (int)((n + kChunk - 1) / kChunk);
-  const int ldp = kMaxRestart + 1;
+  const int ldp = m + 1;
   krylov_alloc(g, m);
   double* normpart = k.partial.get();  // reductions of norms share the partial buffer
   DevBuf<double> np2;                  // separate buffer for the norm partials inside a step
@@ -324,7 +335,7 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
   }
   double rhsnorm = fnorm;
   if (left) {
-    bd_apply(g, f, k.t.get(), nullptr);
+    bd_apply(g, f, k.t.get(), nullptr, precision == STOKES_FP32);
     rhsnorm = device_norm(g, k.t.get(), n);
   }
   const double xnorm0 = device_norm(g, x, n);
@@ -346,7 +357,7 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
     res.relres = rn / fnorm;
     double beta = rn;
     if (left) {
-      bd_apply(g, k.r.get(), k.Z.get(), nullptr);
+      bd_apply(g, k.r.get(), k.Z.get(), nullptr, precision == STOKES_FP32);
       k_copy<<<gv, 256, 0, s>>>(k.r.get(), k.Z.get(), n);
       beta = device_norm(g, k.r.get(), n);
     }
@@ -376,18 +387,19 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
       if (!use_pc) {
         apply_operator(g, vj, k.w.get(), precision, state);
       } else if (!left) {
-        bd_apply(g, vj, k.Z.get(), state);
+        bd_apply(g, vj, k.Z.get(), state, precision == STOKES_FP32);
         apply_operator(g, k.Z.get(), k.w.get(), precision, state);
       } else {
         apply_operator(g, vj, k.t.get(), precision, state);
-        bd_apply(g, k.t.get(), k.w.get(), state);
+        bd_apply(g, k.t.get(), k.w.get(), state, precision == STOKES_FP32);
       }
       const int pa = g.prof.begin(kProfArnoldi, 8.0 * n * (4.0 * (j + 1) + 4.0), s);
       for (int pass = 0; pass < 2; ++pass) {
         k_dot_partial<<<nblk, 256, 0, s>>>(k.V.get(), n, j + 1, k.w.get(), n, k.partial.get(), ldp, state);
-        k_orth_update<<<nblk, 256, 0, s>>>(k.V.get(), n, j + 1, k.partial.get(), ldp, nblk, k.w.get(), n,
-                                           k.H.get() + (int64_t)j * (m + 1), pass, pass ? np2.get() : nullptr,
-                                           state);
+        k_reduce_partials<<<(j + 1 + 255) / 256, 256, 0, s>>>(k.partial.get(), ldp, nblk, j + 1, k.y.get(),
+                                                              k.H.get() + (int64_t)j * (m + 1), pass, state);
+        k_orth_update<<<nblk, 256, 0, s>>>(k.V.get(), n, j + 1, k.y.get(), k.w.get(), n,
+                                           pass ? np2.get() : nullptr, state);
       }
       k_arnoldi_finish<<<1, 32, 0, s>>>(j, m, np2.get(), nblk, k.H.get(), k.cs.get(), k.sn.get(), k.g.get(),
                                         k.scal.get(), state, rhsnorm, tol);
@@ -398,16 +410,17 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
     iter_first[mc] = g.prof.entries.size();
     int hstate[3] = {0, 0, 0};
     STOKES_CUDA(cudaMemcpyAsync(hstate, state, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
-    k_lsq_solve<<<1, 32, 0, s>>>(k.H.get(), m, k.g.get(), state, k.y.get());
+    k_lsq_solve<<<1, 256, 0, s>>>(k.H.get(), m, k.g.get(), state, k.y.get(), k.y.get() + (m + 1));
     k_combine<<<gv, 256, 0, s>>>(k.V.get(), n, k.y.get(), state, k.t.get(), n);
     if (use_pc && !left) {
-      bd_apply(g, k.t.get(), k.Z.get(), nullptr);
+      bd_apply(g, k.t.get(), k.Z.get(), nullptr, precision == STOKES_FP32);
       k_axpy<<<gv, 256, 0, s>>>(x, k.Z.get(), n);
     } else {
       k_axpy<<<gv, 256, 0, s>>>(x, k.t.get(), n);
     }
     STOKES_LAUNCHED();
     STOKES_CUDA(cudaStreamSynchronize(s));
+    bd_check_barrier(g);
     // launches of iterations after convergence returned at once: not timed work
     for (size_t e = iter_first[hstate[1]]; e < iter_first[mc]; ++e) g.prof.entries[e].valid = false;
     iters += hstate[1];
@@ -446,7 +459,7 @@ static SolveResult ir_solve(Geom& g, const double* f, double* x, double tol, int
   r.alloc(n);
   d.alloc(n);
   t.alloc(n);
-  require(restart >= 1 && restart <= kMaxRestart, "restart must be in [1, 1000]");
+  require(restart >= 1 && restart <= kMaxRestart, "restart must be in [1, 8192]");
   krylov_alloc(g, restart);  // device_norm and the residual below use its buffers
   SolveResult res;
   const double fnorm = device_norm(g, f, n);

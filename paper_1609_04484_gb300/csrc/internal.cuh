@@ -93,6 +93,13 @@ struct BlockDiag {
   DevBuf<int> status;             // 0 ok, 1 zero pivot
   DevBuf<double> pv, ivp;         // pivot search scratch
   DevBuf<int64_t> pi;
+  // single-precision copies for the inner solves of the refinement
+  DevBuf<float> inv32;            // inverses (same offsets as lu)
+  DevBuf<float> lu32;             // factors of the triangular-solve blocks, packed
+  std::vector<int64_t> lu32_off;  // per component offset into lu32 (-1 if none)
+  DevBuf<float> work32;           // persistent solve work vector
+  DevBuf<double> work64;
+  DevBuf<unsigned> barrier;       // count, generation, sticky error
 };
 
 // Workspace of the Krylov solver.
@@ -193,6 +200,7 @@ unsigned long long launches_dlp_f64();
 unsigned long long launches_dlp_f32();
 unsigned long long launches_dlp_df64();
 unsigned long long launches_bd();
+unsigned long long launches_bd_trsv();
 unsigned long long launches_gmres();
 
 // ---- geometry.cu ----
@@ -212,7 +220,12 @@ void dlp_apply_df64(Geom& g, const double2* sigma, double2* y, bool boundary,
 
 // ---- bd.cu ----
 void bd_setup(Geom& g);
-void bd_apply(Geom& g, const double* v, double* z, const int* done);
+// f32: use the single-precision inverses and factors (inner solves)
+void bd_apply(Geom& g, const double* v, double* z, const int* done, bool f32 = false);
+void bd_check_barrier(Geom& g);
+template <class T>
+void lu_solve_persistent(Geom& g, const T* A, int64_t m, const int* perm, const double* v, double* z, T* work,
+                         const int* done);
 
 // ---- gmres.cu ----
 struct SolveResult {

@@ -302,3 +302,32 @@ def test_profile_records_pair_launches(S, dev):
         assert nb == iters + cycles and msb > 0
         S.stokes_profile_enable(G.handle, False)
         assert S.stokes_profile_read(G.handle, S.STOKES_PROF_PAIRS_DF64)[0] == 0
+
+
+def test_mixed_refinement_with_triangular_wall_block(S, dev):
+    """Refinement on a geometry whose wall block takes the persistent
+    triangular-solve path (float factors in the inner solves)."""
+    pores = [si.circle_curve((-1.5, 0.1), 0.15, 64), si.circle_curve((1.0, -0.2), 0.2, 64)]
+    g = si.assemble_geometry(pores, si.superellipse_curve(4.0, 1.0, 2200), (4.0, 1.0, 8))
+    f = si.pipe_bc(g).reshape(-1)
+    ref = O.solve_gmres(g, f, tol=1e-12, restart=100)["x"]
+    with S.Geometry(g) as G:
+        S.stokes_precond_setup(G.handle)
+        for prec in (S.STOKES_MIXED_IR, S.STOKES_DF64, S.STOKES_FP64):
+            sig = np.zeros_like(f)
+            code, iters, rr, _ = S.stokes_gmres_solve(G.handle, f, sig, tol=1e-11, restart=100, precision=prec)
+            assert code == S.STOKES_OK and rr <= 1e-11
+            assert rel(sig, ref) < 1e-9
+
+
+def test_unrestarted_gmres_long_basis(S, dev):
+    """A Krylov basis longer than 1000 vectors (no restart) on the
+    1152-node problem without preconditioner."""
+    g = si.cached_geometry("cfg1", 0)
+    f = si.pipe_bc(g).reshape(-1)
+    ref = O.solve_dense(g, f)
+    with S.Geometry(g) as G:
+        sig = np.zeros_like(f)
+        code, iters, rr, _ = S.stokes_gmres_solve(G.handle, f, sig, tol=1e-11, restart=1500, max_iter=1500)
+        assert code == S.STOKES_OK and rr <= 1e-11 and iters < 1500
+        assert rel(sig, ref) < 1e-9
