@@ -308,6 +308,10 @@ static double device_norm(Geom& g, const double* v, int64_t n) {
 // the inner tolerance.
 static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, int restart, int max_iter,
                               int precision, int side, bool inner = false) {
+  // single-precision block inverses for the FP32 operator (STOKES_BD_F32=0
+  // keeps the double-precision ones)
+  static const bool bd_f32_ok = !(std::getenv("STOKES_BD_F32") && std::getenv("STOKES_BD_F32")[0] == '0');
+  const bool bd32 = precision == STOKES_FP32 && bd_f32_ok;
   require(restart >= 1 && restart <= kMaxRestart, "restart must be in [1, 8192]");
   require(max_iter >= 1, "max_iter must be >= 1");
   require(tol > 0 && std::isfinite(tol), "tol must be > 0");
@@ -335,7 +339,7 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
   }
   double rhsnorm = fnorm;
   if (left) {
-    bd_apply(g, f, k.t.get(), nullptr, precision == STOKES_FP32);
+    bd_apply(g, f, k.t.get(), nullptr, bd32);
     rhsnorm = device_norm(g, k.t.get(), n);
   }
   const double xnorm0 = device_norm(g, x, n);
@@ -357,7 +361,7 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
     res.relres = rn / fnorm;
     double beta = rn;
     if (left) {
-      bd_apply(g, k.r.get(), k.Z.get(), nullptr, precision == STOKES_FP32);
+      bd_apply(g, k.r.get(), k.Z.get(), nullptr, bd32);
       k_copy<<<gv, 256, 0, s>>>(k.r.get(), k.Z.get(), n);
       beta = device_norm(g, k.r.get(), n);
     }
@@ -387,11 +391,11 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
       if (!use_pc) {
         apply_operator(g, vj, k.w.get(), precision, state);
       } else if (!left) {
-        bd_apply(g, vj, k.Z.get(), state, precision == STOKES_FP32);
+        bd_apply(g, vj, k.Z.get(), state, bd32);
         apply_operator(g, k.Z.get(), k.w.get(), precision, state);
       } else {
         apply_operator(g, vj, k.t.get(), precision, state);
-        bd_apply(g, k.t.get(), k.w.get(), state, precision == STOKES_FP32);
+        bd_apply(g, k.t.get(), k.w.get(), state, bd32);
       }
       const int pa = g.prof.begin(kProfArnoldi, 8.0 * n * (4.0 * (j + 1) + 4.0), s);
       for (int pass = 0; pass < 2; ++pass) {
@@ -413,7 +417,7 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
     k_lsq_solve<<<1, 256, 0, s>>>(k.H.get(), m, k.g.get(), state, k.y.get(), k.y.get() + (m + 1));
     k_combine<<<gv, 256, 0, s>>>(k.V.get(), n, k.y.get(), state, k.t.get(), n);
     if (use_pc && !left) {
-      bd_apply(g, k.t.get(), k.Z.get(), nullptr, precision == STOKES_FP32);
+      bd_apply(g, k.t.get(), k.Z.get(), nullptr, bd32);
       k_axpy<<<gv, 256, 0, s>>>(x, k.Z.get(), n);
     } else {
       k_axpy<<<gv, 256, 0, s>>>(x, k.t.get(), n);
@@ -425,6 +429,9 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
     for (size_t e = iter_first[hstate[1]]; e < iter_first[mc]; ++e) g.prof.entries[e].valid = false;
     iters += hstate[1];
     x_is_zero = false;
+    if (std::getenv("STOKES_TRACE"))
+      std::fprintf(stderr, "[stokes]   cycle: %d columns, converged flag %d, breakdown %d, relres at start %.3e\n",
+                   hstate[1], hstate[0], hstate[2], res.relres);
     if (inner && hstate[0] && !hstate[2]) {
       res.iters = iters;
       res.relres = res.pc_relres = -1.0;  // not evaluated
@@ -496,8 +503,8 @@ static SolveResult ir_solve(Geom& g, const double* f, double* x, double tol, int
     SolveResult in = gmres_core(g, r.get(), d.get(), inner_tol, restart, max_iter - iters, STOKES_FP32, side,
                                 /*inner=*/true);
     if (std::getenv("STOKES_TRACE"))
-      std::fprintf(stderr, "[stokes] refinement step %d: relres %.3e, inner iterations %d (status %d)\n", outer,
-                   res.relres, in.iters, in.status);
+      std::fprintf(stderr, "[stokes] refinement step %d: relres %.3e, inner tol %.1e, inner iterations %d (status %d)\n",
+                   outer, res.relres, inner_tol, in.iters, in.status);
     iters += in.iters;
     if (in.status == STOKES_EBREAKDOWN) {
       res.status = in.status;
