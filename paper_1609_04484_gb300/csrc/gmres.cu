@@ -312,6 +312,7 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
   // keeps the double-precision ones)
   static const bool bd_f32_ok = !(std::getenv("STOKES_BD_F32") && std::getenv("STOKES_BD_F32")[0] == '0');
   const bool bd32 = precision == STOKES_FP32 && bd_f32_ok;
+  const bool trace = std::getenv("STOKES_TRACE") != nullptr;
   require(restart >= 1 && restart <= kMaxRestart, "restart must be in [1, 8192]");
   require(max_iter >= 1, "max_iter must be >= 1");
   require(tol > 0 && std::isfinite(tol), "tol must be > 0");
@@ -410,6 +411,15 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
       k_scale<<<gv, 256, 0, s>>>(k.w.get(), k.scal.get(), 0, vnext, n, state);
       g.prof.end(pa, s);
       STOKES_LAUNCHED();
+      if (trace && (j + 1) % 100 == 0) {
+        double est = 0.0;
+        int st = 0;
+        STOKES_CUDA(cudaMemcpyAsync(&est, k.scal.get() + 4, sizeof(double), cudaMemcpyDeviceToHost, s));
+        STOKES_CUDA(cudaMemcpyAsync(&st, state, sizeof(int), cudaMemcpyDeviceToHost, s));
+        STOKES_CUDA(cudaStreamSynchronize(s));
+        std::fprintf(stderr, "[stokes]   iteration %d: residual estimate %.3e\n", iters + j + 1, est);
+        if (st) break;
+      }
     }
     iter_first[mc] = g.prof.entries.size();
     int hstate[3] = {0, 0, 0};
