@@ -129,6 +129,12 @@ int stokes_precond_setup(stokes_geom* g, int pc_kind);
  * external Krylov codes). v, z [2N]. STOKES_ESTATE if not set up. */
 int stokes_precond_apply(stokes_geom* g, const double* v, double* z);
 
+/* The same with a choice of stored operator: STOKES_FP64 (the double LU
+ * factors and inverses above) or STOKES_FP32 (float copies of the explicit
+ * inverses of every block, the largest ones inverted from float copies of
+ * their factors; used by the FP32 and DF64 solves). */
+int stokes_precond_apply_prec(stokes_geom* g, const double* v, double* z, int precision);
+
 /* Solve A sigma = f by restarted GMRES (Sec. 4: GMRES of Saad and Schultz,
  * relative-residual tolerance) with the preconditioner of the last
  * stokes_precond_setup call (none if never set up).
@@ -136,8 +142,10 @@ int stokes_precond_apply(stokes_geom* g, const double* v, double* z);
  *   tol     relative residual tolerance (> 0)
  *   restart Krylov dimension per cycle, 1..8192 (basis of restart+1 vectors of 2N doubles)
  *   max_iter total inner iterations (>= 1)
- *   precision STOKES_FP64, STOKES_DF64 (operator arithmetic; Arnoldi, Givens
- *             and the least-squares update always FP64) or STOKES_MIXED_IR
+ *   precision STOKES_FP64, STOKES_FP32, STOKES_DF64 (operator arithmetic;
+ *             Arnoldi, Givens and the least-squares update always FP64; the
+ *             true residual is that of the chosen operator, so FP32 stalls
+ *             near single-precision accuracy) or STOKES_MIXED_IR
  *             (iterative refinement: outer residual with the DF64 operator,
  *             corrections by GMRES on the FP32 operator until its Arnoldi
  *             residual estimate is below max(1e-4, tol / (2 |r| / |f|));

@@ -20,6 +20,7 @@ __all__ = [
     "STOKES_MIXED_IR", "STOKES_PC_NONE", "STOKES_PC_BLOCKDIAG", "STOKES_PC_RIGHT", "STOKES_PC_LEFT",
     "StokesError", "lib", "library_path", "stokes_geometry_create", "stokes_geometry_destroy",
     "stokes_geometry_num_nodes", "stokes_matvec", "stokes_precond_setup", "stokes_precond_apply",
+    "stokes_precond_apply_prec",
     "stokes_gmres_solve", "stokes_eval_velocity", "stokes_last_error", "Geometry",
     "stokes_profile_enable", "stokes_profile_read", "STOKES_PROF_PAIRS_FP64", "STOKES_PROF_PAIRS_FP32",
     "STOKES_PROF_PAIRS_DF64", "STOKES_PROF_EPILOGUE", "STOKES_PROF_BD_APPLY", "STOKES_PROF_ARNOLDI",
@@ -56,6 +57,7 @@ def _load():
         "stokes_matvec": (I, [P, P, P, I]),
         "stokes_precond_setup": (I, [P, I]),
         "stokes_precond_apply": (I, [P, P, P]),
+        "stokes_precond_apply_prec": (I, [P, P, P, I]),
         "stokes_gmres_solve": (I, [P, P, D, I, I, I, I, P, ctypes.POINTER(I), ctypes.POINTER(D),
                                    ctypes.POINTER(D)]),
         "stokes_eval_velocity": (I, [P, P, P, I64, P, I]),
@@ -138,6 +140,12 @@ def stokes_precond_setup(handle, pc_kind=STOKES_PC_BLOCKDIAG):
 def stokes_precond_apply(handle, v, z):
     n2 = 2 * stokes_geometry_num_nodes(handle)
     _check(lib.stokes_precond_apply(ctypes.c_void_p(handle), _ptr(v, count=n2), _ptr(z, count=n2)))
+
+
+def stokes_precond_apply_prec(handle, v, z, precision=STOKES_FP64):
+    n2 = 2 * stokes_geometry_num_nodes(handle)
+    _check(lib.stokes_precond_apply_prec(ctypes.c_void_p(handle), _ptr(v, count=n2), _ptr(z, count=n2),
+                                         int(precision)))
 
 
 def stokes_gmres_solve(handle, f, sigma, tol=1e-8, restart=50, max_iter=2000,

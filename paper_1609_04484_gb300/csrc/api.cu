@@ -130,7 +130,12 @@ int stokes_precond_setup(stokes_geom* h, int pc_kind) {
 }
 
 int stokes_precond_apply(stokes_geom* h, const double* v, double* z) {
+  return stokes_precond_apply_prec(h, v, z, STOKES_FP64);
+}
+
+int stokes_precond_apply_prec(stokes_geom* h, const double* v, double* z, int precision) {
   return guarded([&] {
+    stokes::require(precision == STOKES_FP64 || precision == STOKES_FP32, "precision must be FP64 or FP32");
     Geom& g = handle(h);
     stokes::require(v && z && v != z, "bad array arguments");
     stokes::require(g.bd.ready, "preconditioner not set up", STOKES_ESTATE);
@@ -138,7 +143,7 @@ int stokes_precond_apply(stokes_geom* h, const double* v, double* z) {
     const double* vi = input_view(g, v, n, g.stage_in);
     bool staged;
     double* zo = output_view(g, z, n, g.stage_out, staged);
-    stokes::bd_apply(g, vi, zo, nullptr);
+    stokes::bd_apply(g, vi, zo, nullptr, precision == STOKES_FP32);
     STOKES_LAUNCHED();
     finish_output(g, z, zo, n, staged);
     stokes::bd_check_barrier(g);
@@ -152,8 +157,9 @@ int stokes_gmres_solve(stokes_geom* h, const double* f, double tol, int restart,
   const int rc = guarded([&] {
     Geom& g = handle(h);
     stokes::require(f && sigma && f != sigma, "bad array arguments");
-    stokes::require(precision == STOKES_FP64 || precision == STOKES_DF64 || precision == STOKES_MIXED_IR,
-                    "precision must be FP64, DF64 or MIXED_IR");
+    stokes::require(precision == STOKES_FP64 || precision == STOKES_FP32 || precision == STOKES_DF64 ||
+                        precision == STOKES_MIXED_IR,
+                    "precision must be FP64, FP32, DF64 or MIXED_IR");
     stokes::require(pc_side == STOKES_PC_RIGHT || pc_side == STOKES_PC_LEFT, "bad pc_side");
     const size_t n = 2 * g.N;
     const double* fi = input_view(g, f, n, g.stage_in);
@@ -234,7 +240,7 @@ int stokes_profile_read(stokes_geom* h, int kind, int64_t* launches, double* tot
 int64_t stokes_kernel_launches(void) {
   try {
     return (int64_t)(stokes::launches_geometry() + stokes::launches_dlp_f64() + stokes::launches_dlp_f32() +
-                     stokes::launches_dlp_df64() + stokes::launches_bd() + stokes::launches_bd_trsv() + stokes::launches_gmres());
+                     stokes::launches_dlp_df64() + stokes::launches_bd() + stokes::launches_bd_trsv() + stokes::launches_bd_inv32() + stokes::launches_gmres());
   } catch (...) {
     return -1;
   }

@@ -435,7 +435,7 @@ void bd_init_attributes() {
   STOKES_CUDA(cudaFuncSetAttribute(k_bd_gemv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)(kInv * sizeof(double))));
   STOKES_CUDA(cudaFuncSetAttribute(k_bd_gemv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(kInv * sizeof(double))));
+                                   200 * 1024));
   inited = true;
 }
 
@@ -577,7 +577,13 @@ void bd_setup(Geom& g) {
       k_to_f32<<<(unsigned)std::min<int64_t>((mm + 255) / 256, 152 * 32), 256, 0, s>>>(
           b.lu.get() + b.elem_off[k], b.lu32.get() + b.lu32_off[k], mm);
       STOKES_LAUNCHED();
+      // float explicit inverse for the single-precision applies
+      invert_from_lu32(g, b.lu32.get() + b.lu32_off[k], b.rows[k], b.perm.get() + b.piv_off[k],
+                       b.inv32.get() + b.elem_off[k]);
     }
+    b.d_tri_ids.alloc(b.tri_ids.size());
+    STOKES_CUDA(cudaMemcpyAsync(b.d_tri_ids.get(), b.tri_ids.data(), 4 * b.tri_ids.size(), cudaMemcpyHostToDevice, s));
+    b.max_tri_rows = tri_max;
   }
   g.prof.end(ps, s);
   STOKES_CUDA(cudaStreamSynchronize(s));
@@ -593,7 +599,7 @@ void bd_apply(Geom& g, const double* v, double* z, const int* done, bool f32) {
   const int pb = g.prof.begin(kProfBdApply, wbytes * (double)b.elem_off[g.n_comp] + 32.0 * (double)g.N, s);
   if (!b.inv_ids.empty()) {
     dim3 grid((unsigned)b.inv_ids.size(), (unsigned)((b.max_inv_rows + 63) / 64));
-    const size_t sm = b.max_inv_rows * sizeof(double);
+    const size_t sm = b.max_inv_rows * (f32 ? sizeof(float) : sizeof(double));
     if (f32)
       k_bd_gemv<float><<<grid, 256, sm, s>>>(b.d_inv_ids.get(), b.d_rows.get(), b.d_elem_off.get(),
                                              b.d_node_off.get(), b.inv32.get(), v, z, done);
@@ -602,14 +608,19 @@ void bd_apply(Geom& g, const double* v, double* z, const int* done, bool f32) {
                                               b.d_node_off.get(), b.inv.get(), v, z, done);
     STOKES_LAUNCHED();
   }
-  for (int k : b.tri_ids) {
-    const int64_t m = b.rows[k];
-    const int64_t o = 2 * g.off[k];
-    const int* perm = b.perm.get() + b.piv_off[k];
-    if (f32)
-      lu_solve_persistent<float>(g, b.lu32.get() + b.lu32_off[k], m, perm, v + o, z + o, b.work32.get(), done);
-    else
-      lu_solve_persistent<double>(g, b.lu.get() + b.elem_off[k], m, perm, v + o, z + o, b.work64.get(), done);
+  if (f32 && !b.tri_ids.empty()) {
+    // the largest blocks have float explicit inverses too
+    dim3 grid((unsigned)b.tri_ids.size(), (unsigned)((b.max_tri_rows + 63) / 64));
+    k_bd_gemv<float><<<grid, 256, b.max_tri_rows * sizeof(float), s>>>(
+        b.d_tri_ids.get(), b.d_rows.get(), b.d_elem_off.get(), b.d_node_off.get(), b.inv32.get(), v, z, done);
+    STOKES_LAUNCHED();
+  } else {
+    for (int k : b.tri_ids) {
+      const int64_t m = b.rows[k];
+      const int64_t o = 2 * g.off[k];
+      lu_solve_persistent<double>(g, b.lu.get() + b.elem_off[k], m, b.perm.get() + b.piv_off[k], v + o, z + o,
+                                  b.work64.get(), done);
+    }
   }
   g.prof.end(pb, s);
 }

@@ -87,9 +87,10 @@ k_dlp_pairs_df64(int64_t N, const float2* __restrict__ grid, const float4* __res
       lx.l += X.l - p.z;
       df32 ly = dlp::two_diff(Y.h, p.y);
       ly.l += Y.l - p.w;
-      df32 rx = dlp::two_sum(GX - gq.x, lx.h);
+      // the grid difference is zero or dominates |lx.h| <= 2^-8: FastTwoSum is exact
+      df32 rx = dlp::fast_two_sum(GX - gq.x, lx.h);
       rx.l += lx.l;
-      df32 ry = dlp::two_sum(GY - gq.y, ly.h);
+      df32 ry = dlp::fast_two_sum(GY - gq.y, ly.h);
       ry.l += ly.l;
       // rho^2 = rx^2 + ry^2
       const float px = rx.h * rx.h;
@@ -136,7 +137,10 @@ void dlp_apply_df64(Geom& g, const double2* sigma, double2* y, bool boundary, co
   STOKES_LAUNCHED();
   g.prof.end(pe, g.stream);
   const int pq = g.prof.begin(kProfEpilogue, (double)g.M * (double)T, g.stream);
-  dlp::launch_epilogue<false>(g, T, splits, boundary, targets, sigma, y, done);
+  if (boundary && dlp::ensure_log_table(g))
+    dlp::launch_epilogue<dlp::kCompDF>(g, T, splits, boundary, targets, sigma, y, done);
+  else
+    dlp::launch_epilogue<dlp::kCompF64>(g, T, splits, boundary, targets, sigma, y, done);
   g.prof.end(pq, g.stream);
 }
 

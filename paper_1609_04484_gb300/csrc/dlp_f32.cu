@@ -20,6 +20,8 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
+// Each thread accumulates two targets, i and i + kThreads, so each staged
+// source (two shared-memory loads) feeds two pair evaluations.
 __global__ void __launch_bounds__(kThreads)
 k_dlp_pairs_f32(int64_t N, const float4* __restrict__ src, const float2* __restrict__ lo,
                 const double2* __restrict__ sig, int64_t T, const double2* __restrict__ tgt, int64_t chunk,
@@ -28,15 +30,18 @@ k_dlp_pairs_f32(int64_t N, const float4* __restrict__ src, const float2* __restr
   if (done && *done) return;
   __shared__ float4 s_a[kTile];  // x_hi, y_hi, a_x, a_y
   __shared__ float4 s_b[kTile];  // x_lo, y_lo, sigma_x, sigma_y
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  double2 x = make_double2(0.0, 0.0);
-  if (i < T) x = tgt[i];
-  const float xh = (float)x.x, yh = (float)x.y;
-  const float xl = (float)(x.x - (double)xh), yl = (float)(x.y - (double)yh);
+  const int64_t i0 = blockIdx.x * (int64_t)(2 * kThreads) + threadIdx.x;
+  const int64_t i1 = i0 + kThreads;
+  const double2 x0 = i0 < T ? tgt[i0] : make_double2(0.0, 0.0);
+  const double2 x1 = i1 < T ? tgt[i1] : make_double2(0.0, 0.0);
+  const float xh0 = (float)x0.x, yh0 = (float)x0.y;
+  const float xl0 = (float)(x0.x - (double)xh0), yl0 = (float)(x0.y - (double)yh0);
+  const float xh1 = (float)x1.x, yh1 = (float)x1.y;
+  const float xl1 = (float)(x1.x - (double)xh1), yl1 = (float)(x1.y - (double)yh1);
   const int64_t j0 = blockIdx.y * chunk;
   const int64_t j1 = imin64(N, j0 + chunk);
-  const int64_t iself = self_skip ? i : -1;
-  double ux = 0.0, uy = 0.0;
+  const int64_t is0 = self_skip ? i0 : -1, is1 = self_skip ? i1 : -1;
+  double ux0 = 0.0, uy0 = 0.0, ux1 = 0.0, uy1 = 0.0;
   for (int64_t t0 = j0; t0 < j1; t0 += kTile) {
     __syncthreads();
     for (int q = threadIdx.x; q < kTile; q += blockDim.x) {
@@ -52,27 +57,44 @@ k_dlp_pairs_f32(int64_t N, const float4* __restrict__ src, const float2* __restr
       }
     }
     __syncthreads();
-    const int64_t jb = t0 - iself;
-    float fx = 0.f, fy = 0.f;
-#pragma unroll 8
+    const int64_t jb0 = t0 - is0, jb1 = t0 - is1;
+    float fx0 = 0.f, fy0 = 0.f, fx1 = 0.f, fy1 = 0.f;
+#pragma unroll 4
     for (int q = 0; q < kTile; ++q) {
       const float4 a = s_a[q];
       const float4 b = s_b[q];
-      const float rx = (xh - a.x) + (xl - b.x);
-      const float ry = (yh - a.y) + (yl - b.y);
-      float r2 = fmaf(rx, rx, ry * ry);
-      r2 = (q + jb == 0) ? 1.f : r2;
-      const float inv = rcp_approx(r2);
-      const float d = fmaf(rx, a.z, ry * a.w);
-      const float e = fmaf(rx, b.z, ry * b.w);
-      const float c = (d * inv) * (e * inv);
-      fx = fmaf(c, rx, fx);
-      fy = fmaf(c, ry, fy);
+      {
+        const float rx = (xh0 - a.x) + (xl0 - b.x);
+        const float ry = (yh0 - a.y) + (yl0 - b.y);
+        float r2 = fmaf(rx, rx, ry * ry);
+        r2 = (q + jb0 == 0) ? 1.f : r2;
+        const float inv = rcp_approx(r2);
+        const float d = fmaf(rx, a.z, ry * a.w);
+        const float e = fmaf(rx, b.z, ry * b.w);
+        const float c = (d * inv) * (e * inv);
+        fx0 = fmaf(c, rx, fx0);
+        fy0 = fmaf(c, ry, fy0);
+      }
+      {
+        const float rx = (xh1 - a.x) + (xl1 - b.x);
+        const float ry = (yh1 - a.y) + (yl1 - b.y);
+        float r2 = fmaf(rx, rx, ry * ry);
+        r2 = (q + jb1 == 0) ? 1.f : r2;
+        const float inv = rcp_approx(r2);
+        const float d = fmaf(rx, a.z, ry * a.w);
+        const float e = fmaf(rx, b.z, ry * b.w);
+        const float c = (d * inv) * (e * inv);
+        fx1 = fmaf(c, rx, fx1);
+        fy1 = fmaf(c, ry, fy1);
+      }
     }
-    ux += fx;
-    uy += fy;
+    ux0 += fx0;
+    uy0 += fy0;
+    ux1 += fx1;
+    uy1 += fy1;
   }
-  if (i < T) part[blockIdx.y * T + i] = make_double2(ux, uy);
+  if (i0 < T) part[blockIdx.y * T + i0] = make_double2(ux0, uy0);
+  if (i1 < T) part[blockIdx.y * T + i1] = make_double2(ux1, uy1);
 }
 
 }  // namespace
@@ -83,16 +105,16 @@ void dlp_apply_f32(Geom& g, const double2* sigma, double2* y, bool boundary, con
   moments_f64(g, sigma, done);
   int splits;
   int64_t chunk;
-  dlp::pair_launch_shape(g.N, T, kThreads, kTile, splits, chunk);
+  dlp::pair_launch_shape(g.N, T, 2 * kThreads, kTile, splits, chunk);
   g.part.alloc((size_t)splits * T);
-  dim3 grid((unsigned)((T + kThreads - 1) / kThreads), (unsigned)splits);
+  dim3 grid((unsigned)((T + 2 * kThreads - 1) / (2 * kThreads)), (unsigned)splits);
   const int pe = g.prof.begin(kProfPairsF32, (double)g.N * (double)T, g.stream);
   k_dlp_pairs_f32<<<grid, kThreads, 0, g.stream>>>(g.N, g.f32_src.get(), g.f32_lo.get(), sigma, T, targets, chunk,
                                                     boundary ? 1 : 0, g.part.get(), done);
   STOKES_LAUNCHED();
   g.prof.end(pe, g.stream);
   const int pq = g.prof.begin(kProfEpilogue, (double)g.M * (double)T, g.stream);
-  dlp::launch_epilogue<true>(g, T, splits, boundary, targets, sigma, y, done);
+  dlp::launch_epilogue<dlp::kCompF32>(g, T, splits, boundary, targets, sigma, y, done);
   g.prof.end(pq, g.stream);
 }
 

@@ -78,7 +78,7 @@ void dlp_apply_f64(Geom& g, const double2* sigma, double2* y, bool boundary, con
   STOKES_LAUNCHED();
   g.prof.end(pe, g.stream);
   const int pq = g.prof.begin(kProfEpilogue, (double)g.M * (double)T, g.stream);
-  dlp::launch_epilogue<false>(g, T, splits, boundary, targets, sigma, y, done);
+  dlp::launch_epilogue<dlp::kCompF64>(g, T, splits, boundary, targets, sigma, y, done);
   g.prof.end(pq, g.stream);
 }
 

@@ -308,10 +308,11 @@ static double device_norm(Geom& g, const double* v, int64_t n) {
 // the inner tolerance.
 static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, int restart, int max_iter,
                               int precision, int side, bool inner = false) {
-  // single-precision block inverses for the FP32 operator (STOKES_BD_F32=0
-  // keeps the double-precision ones)
+  // single-precision block inverses for the FP32 and double-float operators
+  // (a fixed linear preconditioner: the converged solution is unchanged);
+  // STOKES_BD_F32=0 keeps the double-precision ones
   static const bool bd_f32_ok = !(std::getenv("STOKES_BD_F32") && std::getenv("STOKES_BD_F32")[0] == '0');
-  const bool bd32 = precision == STOKES_FP32 && bd_f32_ok;
+  const bool bd32 = (precision == STOKES_FP32 || precision == STOKES_DF64) && bd_f32_ok;
   const bool trace = std::getenv("STOKES_TRACE") != nullptr;
   require(restart >= 1 && restart <= kMaxRestart, "restart must be in [1, 8192]");
   require(max_iter >= 1, "max_iter must be >= 1");

@@ -98,6 +98,8 @@ struct BlockDiag {
   DevBuf<float> lu32;             // factors of the triangular-solve blocks, packed
   std::vector<int64_t> lu32_off;  // per component offset into lu32 (-1 if none)
   DevBuf<float> work32;           // persistent solve work vector
+  DevBuf<int> d_tri_ids;          // blocks applied by triangular solves in FP64
+  int64_t max_tri_rows = 0;
   DevBuf<double> work64;
   DevBuf<unsigned> barrier;       // count, generation, sticky error
 };
@@ -183,6 +185,10 @@ struct Geom {
   DevBuf<float4> df_pos;    // remainder x - grid as a float pair: rx_hi, ry_hi, rx_lo, ry_lo
   DevBuf<float4> df_a;      // a_x hi, a_y hi, a_x lo, a_y lo  (a = w n / pi)
 
+  // log |x_i - c_k|^2 for every node and pore (double-float completion)
+  DevBuf<float2> logtab;
+  bool logtab_ready = false;
+
   // workspaces
   DevBuf<double4_32a> mom;    // lambda_x, lambda_y, xi, s0 per component
   DevBuf<double2> part;   // split partial sums of the pair kernel
@@ -201,6 +207,7 @@ unsigned long long launches_dlp_f32();
 unsigned long long launches_dlp_df64();
 unsigned long long launches_bd();
 unsigned long long launches_bd_trsv();
+unsigned long long launches_bd_inv32();
 unsigned long long launches_gmres();
 
 // ---- geometry.cu ----
@@ -223,6 +230,7 @@ void bd_setup(Geom& g);
 // f32: use the single-precision inverses and factors (inner solves)
 void bd_apply(Geom& g, const double* v, double* z, const int* done, bool f32 = false);
 void bd_check_barrier(Geom& g);
+void invert_from_lu32(Geom& g, const float* LU, int64_t m, const int* perm, float* X);
 template <class T>
 void lu_solve_persistent(Geom& g, const T* A, int64_t m, const int* perm, const double* v, double* z, T* work,
                          const int* done);

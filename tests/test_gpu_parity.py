@@ -221,6 +221,21 @@ def test_block_diagonal_large_wall_block_triangular_path(S, dev):
         assert rel(z, ref) < 1e-11
 
 
+def test_block_diagonal_float_inverses(S, dev):
+    """The float explicit inverses (including a wall block inverted by the
+    blocked float triangular inversion) match the oracle to single
+    precision times the blocks' conditioning (1e-4)."""
+    pores = [si.circle_curve((-1.5, 0.1), 0.15, 64), si.circle_curve((1.0, -0.2), 0.2, 64)]
+    g = si.assemble_geometry(pores, si.superellipse_curve(4.0, 1.0, 2200), (4.0, 1.0, 8))
+    v = np.random.default_rng(9).standard_normal(2 * g.n_nodes)
+    ref = O.BlockDiagonal(g).apply(v)
+    with S.Geometry(g) as G:
+        S.stokes_precond_setup(G.handle)
+        z = np.empty_like(v)
+        S.stokes_precond_apply_prec(G.handle, v, z, S.STOKES_FP32)
+        assert rel(z, ref) < 1e-4
+
+
 def test_full_size_block_diagonal_sampled_rows(S, dev):
     """136,192-node geometry: for sampled rows i of each sampled block k,
     (A_kk z_k)_i equals v_i, with A_kk's rows from the oracle."""
