@@ -53,6 +53,10 @@ def parse_args():
     p.add_argument("--targets", type=int, default=4096)
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--kernel-bench", action="store_true",
+                   help="time only operator applications (A sigma) of each precision on the workload")
+    p.add_argument("--reps", type=int, default=5)
+    p.add_argument("--precisions", default="fp32,df64,fp64")
     return p.parse_args()
 
 
@@ -189,8 +193,52 @@ def run_reference(args):
 # GPU leg
 # ---------------------------------------------------------------------------
 
+def kernel_bench(args):
+    """A sigma on the workload for each precision; prints one JSON line per
+    precision with the pair kernel's device time from the library's event
+    timing (also the entry point used for ncu captures)."""
+    import torch
+    import paper_1609_04484_gb300 as S
+    import stokes_inputs as si
+    dev = torch.device("cuda", 0)
+    geom = si.cached_geometry(args.workload, 0)
+    stream = torch.cuda.current_stream(dev)
+    G = S.Geometry(geom, stream=stream.cuda_stream)
+    sig = torch.tensor(si.random_density(geom, 1).reshape(-1), device=dev)
+    y = torch.empty_like(sig)
+    kinds = {"fp32": (S.STOKES_FP32, S.STOKES_PROF_PAIRS_FP32, "k_dlp_pairs_f32"),
+             "df64": (S.STOKES_DF64, S.STOKES_PROF_PAIRS_DF64, "k_dlp_pairs_df64"),
+             "fp64": (S.STOKES_FP64, S.STOKES_PROF_PAIRS_FP64, "k_dlp_pairs_f64")}
+    for name in args.precisions.split(","):
+        prec, kind, kname = kinds[name]
+        for _ in range(args.warmup):
+            S.stokes_matvec(G.handle, sig, y, prec)
+        torch.cuda.synchronize()
+        S.stokes_profile_enable(G.handle, True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.reps):
+            S.stokes_matvec(G.handle, sig, y, prec)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        n, ms, pairs = S.stokes_profile_read(G.handle, kind)
+        ne, mse, _ = S.stokes_profile_read(G.handle, S.STOKES_PROF_EPILOGUE)
+        S.stokes_profile_enable(G.handle, False)
+        avg = ms / n
+        gp = pairs / n / (avg * 1e-3)
+        print(json.dumps({"kernel": kname, "precision": name, "workload": workload_config(args.workload)["workload"],
+                          "matvec_ms": round(ev0.elapsed_time(ev1) / args.reps, 3),
+                          "pair_kernel_ms": round(avg, 3), "epilogue_ms": round(mse / max(ne, 1), 3),
+                          "gpairs_per_s": round(gp / 1e9, 1),
+                          "tflops_18_per_pair": round(FLOPS_PER_PAIR * gp / 1e12, 3)}), flush=True)
+    G.close()
+
+
 def main():
     args = parse_args()
+    if args.kernel_bench:
+        kernel_bench(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
