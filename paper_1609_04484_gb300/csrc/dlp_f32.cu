@@ -25,7 +25,7 @@ __device__ __forceinline__ float rcp_approx(float x) {
 __global__ void __launch_bounds__(kThreads)
 k_dlp_pairs_f32(int64_t N, const float4* __restrict__ src, const float2* __restrict__ lo,
                 const double2* __restrict__ sig, int64_t T, const double2* __restrict__ tgt, int64_t chunk,
-                int self_skip, double2* __restrict__ part, const int* __restrict__ done) {
+                double2* __restrict__ part, const int* __restrict__ done) {
   count_launch();
   if (done && *done) return;
   __shared__ float4 s_a[kTile];  // x_hi, y_hi, a_x, a_y
@@ -40,7 +40,6 @@ k_dlp_pairs_f32(int64_t N, const float4* __restrict__ src, const float2* __restr
   const float xl1 = (float)(x1.x - (double)xh1), yl1 = (float)(x1.y - (double)yh1);
   const int64_t j0 = blockIdx.y * chunk;
   const int64_t j1 = imin64(N, j0 + chunk);
-  const int64_t is0 = self_skip ? i0 : -1, is1 = self_skip ? i1 : -1;
   double ux0 = 0.0, uy0 = 0.0, ux1 = 0.0, uy1 = 0.0;
   for (int64_t t0 = j0; t0 < j1; t0 += kTile) {
     __syncthreads();
@@ -57,7 +56,6 @@ k_dlp_pairs_f32(int64_t N, const float4* __restrict__ src, const float2* __restr
       }
     }
     __syncthreads();
-    const int64_t jb0 = t0 - is0, jb1 = t0 - is1;
     float fx0 = 0.f, fy0 = 0.f, fx1 = 0.f, fy1 = 0.f;
 #pragma unroll 4
     for (int q = 0; q < kTile; ++q) {
@@ -66,8 +64,9 @@ k_dlp_pairs_f32(int64_t N, const float4* __restrict__ src, const float2* __restr
       {
         const float rx = (xh0 - a.x) + (xl0 - b.x);
         const float ry = (yh0 - a.y) + (yl0 - b.y);
-        float r2 = fmaf(rx, rx, ry * ry);
-        r2 = (q + jb0 == 0) ? 1.f : r2;
+        // + 1e-30: the self pair (r = 0, so d = e = 0) gives a finite inverse
+        // and contributes exactly 0; for any other pair rho^2 >> 1e-30
+        const float r2 = fmaf(rx, rx, fmaf(ry, ry, 1e-30f));
         const float inv = rcp_approx(r2);
         const float d = fmaf(rx, a.z, ry * a.w);
         const float e = fmaf(rx, b.z, ry * b.w);
@@ -78,8 +77,7 @@ k_dlp_pairs_f32(int64_t N, const float4* __restrict__ src, const float2* __restr
       {
         const float rx = (xh1 - a.x) + (xl1 - b.x);
         const float ry = (yh1 - a.y) + (yl1 - b.y);
-        float r2 = fmaf(rx, rx, ry * ry);
-        r2 = (q + jb1 == 0) ? 1.f : r2;
+        const float r2 = fmaf(rx, rx, fmaf(ry, ry, 1e-30f));
         const float inv = rcp_approx(r2);
         const float d = fmaf(rx, a.z, ry * a.w);
         const float e = fmaf(rx, b.z, ry * b.w);
@@ -110,7 +108,7 @@ void dlp_apply_f32(Geom& g, const double2* sigma, double2* y, bool boundary, con
   dim3 grid((unsigned)((T + 2 * kThreads - 1) / (2 * kThreads)), (unsigned)splits);
   const int pe = g.prof.begin(kProfPairsF32, (double)g.N * (double)T, g.stream);
   k_dlp_pairs_f32<<<grid, kThreads, 0, g.stream>>>(g.N, g.f32_src.get(), g.f32_lo.get(), sigma, T, targets, chunk,
-                                                    boundary ? 1 : 0, g.part.get(), done);
+                                                    g.part.get(), done);
   STOKES_LAUNCHED();
   g.prof.end(pe, g.stream);
   const int pq = g.prof.begin(kProfEpilogue, (double)g.M * (double)T, g.stream);
