@@ -390,3 +390,124 @@ def solve_gmres(geom, f, tol=1e-8, restart=50, max_iter=2000, precond="bd", side
         apply_A = lambda v: matvec(geom, v)
     M = BlockDiagonal(geom).apply if precond == "bd" else None
     return gmres(apply_A, f, tol=tol, restart=restart, max_iter=max_iter, apply_M=M, side=side)
+
+
+# ---------------------------------------------------------------------------
+# Two-grid preconditioner and flexible GMRES (not in the paper: the GPU
+# library's alternative to block-diagonal preconditioning, checked here)
+# ---------------------------------------------------------------------------
+
+def trig_interpolation(nc, nf):
+    """(nf x nc) matrix of trigonometric interpolation from nc equispaced
+    samples s_j = 2 pi j / nc of a periodic function to nf samples
+    t_i = 2 pi i / nf: the real trigonometric interpolant
+        P[i, j] = (1/nc) [1 + 2 sum_{k=1}^{K} cos(k (t_i - s_j)) (+ cos((nc/2)(t_i - s_j)) if nc even)],
+    K = ceil(nc / 2) - 1 (the Nyquist cosine split evenly between +-nc/2)."""
+    t = 2.0 * np.pi * np.arange(nf) / nf
+    s = 2.0 * np.pi * np.arange(nc) / nc
+    d = t[:, None] - s[None, :]
+    P = np.ones((nf, nc))
+    for k in range(1, (nc + 1) // 2):
+        P += 2.0 * np.cos(k * d)
+    if nc % 2 == 0:
+        P += np.cos((nc // 2) * d)
+    return P / nc
+
+
+def coarse_geometry(geom, q):
+    """Every q-th node of every component, weights times q (the trapezoid
+    rule on a q-times coarser equispaced parameter grid)."""
+    import dataclasses
+    idx = np.concatenate([np.arange(geom.offsets[k], geom.offsets[k + 1], q) for k in range(geom.n_comp)])
+    sizes = np.diff(geom.offsets) // q
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    return dataclasses.replace(geom, nodes=geom.nodes[idx].copy(), normals=geom.normals[idx].copy(),
+                               weights=geom.weights[idx] * q, curvature=geom.curvature[idx].copy(),
+                               offsets=offs)
+
+
+class TwoGrid:
+    """P^-1 r = I Ac^-1 R r + B^-1 (r - I R r): an exact solve with the same
+    operator on the q-times coarser grid, plus the pores' diagonal blocks on
+    what the coarse grid cannot represent; on the wall the remainder is
+    scaled by -2 (the inverse of the jump -1/2). I is trigonometric
+    interpolation per component, R = (nc / nf) I^T."""
+
+    def __init__(self, geom, q):
+        import scipy.linalg as sla
+        if any(int(n) % q or int(n) // q < 8 for n in np.diff(geom.offsets)):
+            raise ValueError("every component needs a multiple of q nodes, at least 8 q")
+        self.geom = geom
+        self.gc = coarse_geometry(geom, q)
+        self.lu = sla.lu_factor(assemble(self.gc))
+        blocks = []
+        for k in range(geom.n_comp):
+            nf = int(geom.offsets[k + 1] - geom.offsets[k])
+            blocks.append(trig_interpolation(nf // q, nf))
+        Inode = sla.block_diag(*blocks)
+        Rnode = sla.block_diag(*[B.T * (B.shape[1] / B.shape[0]) for B in blocks])
+        self.I = np.kron(Inode, np.eye(2))
+        self.R = np.kron(Rnode, np.eye(2))
+        self.bd = BlockDiagonal(geom)
+        self.wall = slice(2 * int(geom.offsets[geom.outer_comp]), 2 * int(geom.offsets[geom.outer_comp + 1]))
+
+    def apply(self, r):
+        import scipy.linalg as sla
+        r = np.asarray(r, dtype=np.float64).reshape(-1)
+        rc = self.R @ r
+        zc = sla.lu_solve(self.lu, rc)
+        h = r - self.I @ rc
+        zh = self.bd.apply(h)
+        zh[self.wall] = -2.0 * h[self.wall]
+        return self.I @ zc + zh
+
+
+def fgmres(apply_A, f, apply_M, tol=1e-8, restart=200, max_iter=2000):
+    """Flexible GMRES (Saad 1993): the preconditioned vectors z_j = M(v_j)
+    are kept and the iterate is x0 + Z y, so M may vary between steps
+    (rounding inside it included). Stops on the true relative residual."""
+    f = np.asarray(f, dtype=np.float64).reshape(-1)
+    n = f.size
+    x = np.zeros(n)
+    fnorm = np.linalg.norm(f)
+    iters = 0
+    while True:
+        r = f - apply_A(x)
+        beta = np.linalg.norm(r)
+        if beta <= tol * fnorm or iters >= max_iter:
+            return dict(x=x, iters=iters, relres=beta / fnorm)
+        m = min(restart, max_iter - iters)
+        V = np.zeros((m + 1, n))
+        Z = np.zeros((m, n))
+        H = np.zeros((m + 1, m))
+        cs, sn, g = np.zeros(m), np.zeros(m), np.zeros(m + 1)
+        V[0] = r / beta
+        g[0] = beta
+        jd = 0
+        for j in range(m):
+            Z[j] = apply_M(V[j])
+            w = apply_A(Z[j])
+            for i in range(j + 1):
+                H[i, j] = V[i] @ w
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            if H[j + 1, j] > 0:
+                V[j + 1] = w / H[j + 1, j]
+            for i in range(j):
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            den = math.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / den, H[j + 1, j] / den
+            H[j, j] = den
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            iters += 1
+            jd = j + 1
+            if abs(g[j + 1]) <= tol * fnorm:
+                break
+        y = np.zeros(jd)
+        for i in range(jd - 1, -1, -1):
+            y[i] = (g[i] - H[i, i + 1:jd] @ y[i + 1:]) / H[i, i]
+        x = x + Z[:jd].T @ y

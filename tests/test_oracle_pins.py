@@ -232,3 +232,54 @@ def test_pipe_flow_no_net_flux_around_a_pore(cfg1_geom):
     # when evaluated just inside the wall near the intake centre
     x0 = np.array([[-3.9, 0.0]])
     assert abs(O.velocity(g, s, x0)[0, 0] - 1.0) < 0.05
+
+
+def test_trig_interpolation_is_exact_for_band_limited_data():
+    """The interpolation of the two-grid preconditioner reproduces every
+    trigonometric polynomial the coarse grid resolves, and the coarse
+    samples themselves."""
+    for nc, nf in ((8, 32), (16, 128), (9, 27)):
+        P = O.trig_interpolation(nc, nf)
+        t = 2 * np.pi * np.arange(nf) / nf
+        s = 2 * np.pi * np.arange(nc) / nc
+        for k in range((nc + 1) // 2):
+            for fn in (np.cos, np.sin):
+                assert np.abs(P @ fn(k * s) - fn(k * t)).max() < 1e-13
+        assert np.abs(P[:: nf // nc] - np.eye(nc)).max() < 1e-13 if nf % nc == 0 else True
+
+
+def test_coarse_geometry_is_the_trapezoid_rule_on_every_qth_node(small_geom):
+    g = small_geom
+    gc = O.coarse_geometry(g, 4)
+    for k in range(g.n_comp):
+        assert abs(gc.weights[gc.comp_slice(k)].sum() - g.weights[g.comp_slice(k)].sum()) < 1e-12
+    # a smooth integrand integrates to the same value on both grids
+    fx = np.cos(g.nodes[:, 0]) * g.nodes[:, 1] ** 2
+    fc = np.cos(gc.nodes[:, 0]) * gc.nodes[:, 1] ** 2
+    assert abs((g.weights * fx).sum() - (gc.weights * fc).sum()) < 1e-4
+
+
+def test_two_grid_fgmres_solves_the_dense_system_faster_than_block_diagonal():
+    g = si.config1_geometry(0, n_outer=256, n_pores=6, n_per_pore=32)
+    f = si.pipe_bc(g).reshape(-1)
+    A = O.assemble(g)
+    ref = np.linalg.solve(A, f)
+    tg = O.TwoGrid(g, 4)
+    r = O.fgmres(lambda v: A @ v, f, tg.apply, tol=1e-12)
+    assert r["relres"] <= 1e-12 and np.linalg.norm(r["x"] - ref) < 1e-10 * np.linalg.norm(ref)
+    rb = O.solve_gmres(g, f, tol=1e-12, restart=200)
+    assert r["iters"] < 0.6 * rb["iters"]
+
+
+def test_fgmres_tolerates_a_varying_preconditioner(small_geom):
+    """Flexible GMRES (the iterate is built from the stored preconditioned
+    vectors) still converges when the preconditioner changes each step."""
+    g = small_geom
+    f = si.pipe_bc(g).reshape(-1)
+    A = O.assemble(g)
+    bd = O.BlockDiagonal(g)
+    rng = np.random.default_rng(3)
+    noisy = lambda v: bd.apply(v) * (1.0 + 1e-3 * rng.standard_normal(v.size))
+    r = O.fgmres(lambda v: A @ v, f, noisy, tol=1e-11, restart=100)
+    assert r["relres"] <= 1e-11
+    assert np.linalg.norm(r["x"] - np.linalg.solve(A, f)) < 1e-9 * np.linalg.norm(r["x"])
