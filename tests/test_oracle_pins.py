@@ -253,10 +253,12 @@ def test_coarse_geometry_is_the_trapezoid_rule_on_every_qth_node(small_geom):
     gc = O.coarse_geometry(g, 4)
     for k in range(g.n_comp):
         assert abs(gc.weights[gc.comp_slice(k)].sum() - g.weights[g.comp_slice(k)].sum()) < 1e-12
-    # a smooth integrand integrates to the same value on both grids
-    fx = np.cos(g.nodes[:, 0]) * g.nodes[:, 1] ** 2
-    fc = np.cos(gc.nodes[:, 0]) * gc.nodes[:, 1] ** 2
-    assert abs((g.weights * fx).sum() - (gc.weights * fc).sum()) < 1e-4
+    # on each circular pore the coarse rule integrates (x - c_x)^2 exactly:
+    # the integral is pi R^3
+    for k in range(g.n_pores):
+        sl = gc.comp_slice(k)
+        val = (gc.weights[sl] * (gc.nodes[sl, 0] - g.centres[k, 0]) ** 2).sum()
+        assert abs(val - math.pi * g.radii[k] ** 3) < 1e-14
 
 
 def test_two_grid_fgmres_solves_the_dense_system_faster_than_block_diagonal():
