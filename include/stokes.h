@@ -78,7 +78,7 @@ enum stokes_precision {
   STOKES_MIXED_IR = 3
 };
 
-enum stokes_pc_kind { STOKES_PC_NONE = 0, STOKES_PC_BLOCKDIAG = 1 };
+enum stokes_pc_kind { STOKES_PC_NONE = 0, STOKES_PC_BLOCKDIAG = 1, STOKES_PC_TWOGRID = 2 };
 enum stokes_pc_side { STOKES_PC_RIGHT = 0, STOKES_PC_LEFT = 1 };
 
 typedef struct stokes_geom stokes_geom;
@@ -125,8 +125,27 @@ int stokes_matvec(stokes_geom* g, const double* sigma, double* y, int precision)
  * (zero pivot) gives STOKES_EBREAKDOWN. */
 int stokes_precond_setup(stokes_geom* g, int pc_kind);
 
-/* z = P^-1 v with the block-diagonal preconditioner (for tests and
- * external Krylov codes). v, z [2N]. STOKES_ESTATE if not set up. */
+/* Two-grid preconditioner (the paper has no counterpart: a GPU-native
+ * alternative to its block-diagonal baseline for densely packed pores):
+ *   P^-1 r = I Ac^-1 R r + B^-1 (r - I R r)
+ * Ac is the operator above on the coarse grid made of every `coarsen`-th
+ * node of every component with weights times `coarsen` (the trapezoid rule
+ * on a coarser equispaced parameter grid), assembled densely on the GPU and
+ * LU-factorised with partial pivoting in single precision; I is the real
+ * trigonometric interpolation of each component's coarse samples (Nyquist
+ * cosine split evenly), R = (n_coarse / n_fine) I^T; B^-1 are the pores'
+ * diagonal blocks (as in stokes_precond_setup) and -2 I on the wall.
+ * Requires every component's node count to be a multiple of `coarsen` with
+ * at least 8 coarse nodes, and nodes equispaced in the curve's parameter
+ * (the trapezoid rule of Sec. 2.2). Replaces any previous preconditioner;
+ * stokes_gmres_solve then runs flexible GMRES, right side only.
+ * Memory: 16 (N / coarsen)^2 bytes for the coarse factors.
+ * Errors: STOKES_EINVAL (sizes), STOKES_ENOMEM, STOKES_EBREAKDOWN (zero
+ * pivot), STOKES_ECUDA. */
+int stokes_precond_setup_twogrid(stokes_geom* g, int coarsen);
+
+/* z = P^-1 v with the current preconditioner (for tests and external
+ * Krylov codes). v, z [2N]. STOKES_ESTATE if not set up. */
 int stokes_precond_apply(stokes_geom* g, const double* v, double* z);
 
 /* The same with a choice of stored operator: STOKES_FP64 (the double LU
@@ -137,7 +156,10 @@ int stokes_precond_apply_prec(stokes_geom* g, const double* v, double* z, int pr
 
 /* Solve A sigma = f by restarted GMRES (Sec. 4: GMRES of Saad and Schultz,
  * relative-residual tolerance) with the preconditioner of the last
- * stokes_precond_setup call (none if never set up).
+ * stokes_precond_setup* call (none if never set up). With a right
+ * preconditioner the solver keeps the preconditioned basis vectors
+ * (flexible GMRES), so preconditioners that round to single precision are
+ * safe; the stop is always on the true residual.
  *   f       [2N] right-hand side (the boundary data at the nodes)
  *   tol     relative residual tolerance (> 0)
  *   restart Krylov dimension per cycle, 1..8192 (basis of restart+1 vectors of 2N doubles)

@@ -20,7 +20,7 @@ __all__ = [
     "STOKES_MIXED_IR", "STOKES_PC_NONE", "STOKES_PC_BLOCKDIAG", "STOKES_PC_RIGHT", "STOKES_PC_LEFT",
     "StokesError", "lib", "library_path", "stokes_geometry_create", "stokes_geometry_destroy",
     "stokes_geometry_num_nodes", "stokes_matvec", "stokes_precond_setup", "stokes_precond_apply",
-    "stokes_precond_apply_prec",
+    "stokes_precond_apply_prec", "stokes_precond_setup_twogrid", "STOKES_PC_TWOGRID",
     "stokes_gmres_solve", "stokes_eval_velocity", "stokes_last_error", "Geometry",
     "stokes_profile_enable", "stokes_profile_read", "STOKES_PROF_PAIRS_FP64", "STOKES_PROF_PAIRS_FP32",
     "STOKES_PROF_PAIRS_DF64", "STOKES_PROF_EPILOGUE", "STOKES_PROF_BD_APPLY", "STOKES_PROF_ARNOLDI",
@@ -30,7 +30,7 @@ __all__ = [
 STOKES_OK, STOKES_EINVAL, STOKES_ENOMEM, STOKES_ECUDA = 0, -1, -2, -3
 STOKES_ENOTCONV, STOKES_EBREAKDOWN, STOKES_ESTATE = -4, -5, -6
 STOKES_FP64, STOKES_FP32, STOKES_DF64, STOKES_MIXED_IR = 0, 1, 2, 3
-STOKES_PC_NONE, STOKES_PC_BLOCKDIAG = 0, 1
+STOKES_PC_NONE, STOKES_PC_BLOCKDIAG, STOKES_PC_TWOGRID = 0, 1, 2
 STOKES_PC_RIGHT, STOKES_PC_LEFT = 0, 1
 (STOKES_PROF_PAIRS_FP64, STOKES_PROF_PAIRS_FP32, STOKES_PROF_PAIRS_DF64, STOKES_PROF_EPILOGUE,
  STOKES_PROF_BD_APPLY, STOKES_PROF_ARNOLDI, STOKES_PROF_BD_SETUP) = range(7)
@@ -56,6 +56,7 @@ def _load():
         "stokes_geometry_num_nodes": (I64, [P]),
         "stokes_matvec": (I, [P, P, P, I]),
         "stokes_precond_setup": (I, [P, I]),
+        "stokes_precond_setup_twogrid": (I, [P, I]),
         "stokes_precond_apply": (I, [P, P, P]),
         "stokes_precond_apply_prec": (I, [P, P, P, I]),
         "stokes_gmres_solve": (I, [P, P, D, I, I, I, I, P, ctypes.POINTER(I), ctypes.POINTER(D),
@@ -135,6 +136,10 @@ def stokes_matvec(handle, sigma, y, precision=STOKES_FP64):
 
 def stokes_precond_setup(handle, pc_kind=STOKES_PC_BLOCKDIAG):
     _check(lib.stokes_precond_setup(ctypes.c_void_p(handle), int(pc_kind)))
+
+
+def stokes_precond_setup_twogrid(handle, coarsen=8):
+    _check(lib.stokes_precond_setup_twogrid(ctypes.c_void_p(handle), int(coarsen)))
 
 
 def stokes_precond_apply(handle, v, z):

@@ -119,13 +119,25 @@ int stokes_precond_setup(stokes_geom* h, int pc_kind) {
   return guarded([&] {
     Geom& g = handle(h);
     stokes::require(pc_kind == STOKES_PC_NONE || pc_kind == STOKES_PC_BLOCKDIAG, "unknown pc_kind");
+    g.tg.ready = false;
+    g.bd.ready = false;
     if (pc_kind == STOKES_PC_NONE) {
-      g.bd.ready = false;
       g.bd.lu.release();
       g.bd.inv.release();
+      g.tg.lu.release();
       return;
     }
+    g.tg.lu.release();
     stokes::bd_setup(g);
+  });
+}
+
+int stokes_precond_setup_twogrid(stokes_geom* h, int coarsen) {
+  return guarded([&] {
+    Geom& g = handle(h);
+    g.tg.ready = false;
+    g.bd.ready = false;
+    stokes::twogrid_setup(g, coarsen);
   });
 }
 
@@ -138,12 +150,12 @@ int stokes_precond_apply_prec(stokes_geom* h, const double* v, double* z, int pr
     stokes::require(precision == STOKES_FP64 || precision == STOKES_FP32, "precision must be FP64 or FP32");
     Geom& g = handle(h);
     stokes::require(v && z && v != z, "bad array arguments");
-    stokes::require(g.bd.ready, "preconditioner not set up", STOKES_ESTATE);
+    stokes::require(g.bd.ready || g.tg.ready, "preconditioner not set up", STOKES_ESTATE);
     const size_t n = 2 * g.N;
     const double* vi = input_view(g, v, n, g.stage_in);
     bool staged;
     double* zo = output_view(g, z, n, g.stage_out, staged);
-    stokes::bd_apply(g, vi, zo, nullptr, precision == STOKES_FP32);
+    stokes::precond_apply(g, vi, zo, nullptr, precision == STOKES_FP32);
     STOKES_LAUNCHED();
     finish_output(g, z, zo, n, staged);
     stokes::bd_check_barrier(g);
@@ -240,7 +252,8 @@ int stokes_profile_read(stokes_geom* h, int kind, int64_t* launches, double* tot
 int64_t stokes_kernel_launches(void) {
   try {
     return (int64_t)(stokes::launches_geometry() + stokes::launches_dlp_f64() + stokes::launches_dlp_f32() +
-                     stokes::launches_dlp_df64() + stokes::launches_bd() + stokes::launches_bd_trsv() + stokes::launches_bd_inv32() + stokes::launches_gmres());
+                     stokes::launches_dlp_df64() + stokes::launches_bd() + stokes::launches_bd_trsv() + stokes::launches_bd_inv32() + stokes::launches_twogrid() +
+                     stokes::launches_gmres());
   } catch (...) {
     return -1;
   }

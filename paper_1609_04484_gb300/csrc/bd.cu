@@ -392,7 +392,7 @@ k_inv_from_lu(const double* __restrict__ A, int64_t m, const int* __restrict__ p
 // z_k = X_k v_k for the blocks in `ids`; CTA (b, s) computes rows
 // [64 s, 64 s + 64) of block ids[b]; the 256 threads split the columns in
 // four interleaved phases and combine them in shared memory.
-template <class T>
+template <class T, bool kAcc = false>
 __global__ void __launch_bounds__(256)
 k_bd_gemv(const int* __restrict__ ids, const int64_t* __restrict__ rows,
           const int64_t* __restrict__ elem_off, const int64_t* __restrict__ node_off,
@@ -418,7 +418,11 @@ k_bd_gemv(const int* __restrict__ ids, const int64_t* __restrict__ rows,
     for (int64_t q = ph; q < m; q += 4) acc += Xk[q * m + r] * sv[q];
   red[ph][rr] = acc;
   __syncthreads();
-  if (ph == 0 && r < m) z[2 * node_off[k] + r] = (double)((red[0][rr] + red[1][rr]) + (red[2][rr] + red[3][rr]));
+  if (ph == 0 && r < m) {
+    const double val = (double)((red[0][rr] + red[1][rr]) + (red[2][rr] + red[3][rr]));
+    double* zp = z + 2 * node_off[k] + r;
+    *zp = kAcc ? *zp + val : val;
+  }
 }
 
 __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
@@ -436,10 +440,22 @@ void bd_init_attributes() {
                                    (int)(kInv * sizeof(double))));
   STOKES_CUDA(cudaFuncSetAttribute(k_bd_gemv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    200 * 1024));
+  STOKES_CUDA(cudaFuncSetAttribute(k_bd_gemv<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(kInv * sizeof(double))));
+  STOKES_CUDA(cudaFuncSetAttribute(k_bd_gemv<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   200 * 1024));
   inited = true;
 }
 
-void bd_setup(Geom& g) {
+static void bd_setup_impl(Geom& g, bool skip_wall);
+
+void bd_setup(Geom& g) { bd_setup_impl(g, false); }
+
+// Blocks of the pores only (the wall is left out): used next to the
+// two-grid coarse solve.
+void bd_setup_pores(Geom& g, bool skip_wall) { bd_setup_impl(g, skip_wall); }
+
+static void bd_setup_impl(Geom& g, bool skip_wall) {
   bd_init_attributes();
   BlockDiag& b = g.bd;
   b.ready = false;
@@ -458,18 +474,19 @@ void bd_setup(Geom& g) {
   b.inv_ids.clear();
   b.tri_ids.clear();
   for (int k = 0; k < nc; ++k) {
-    const int64_t m = 2 * (g.off[k + 1] - g.off[k]);
+    const int64_t m = (skip_wall && k == g.outer) ? 0 : 2 * (g.off[k + 1] - g.off[k]);
     b.rows[k] = m;
     b.elem_off[k + 1] = b.elem_off[k] + m * m;
     b.piv_off[k + 1] = b.piv_off[k] + m;
+    if (m == 0) continue;
     if (m <= kSmall) b.small_ids.push_back(k);
     (m <= kInv ? b.inv_ids : b.tri_ids).push_back(k);
     b.max_inv_rows = 0;
   }
   for (int k : b.inv_ids) b.max_inv_rows = std::max(b.max_inv_rows, b.rows[k]);
   const int64_t total = b.elem_off[nc];
-  b.lu.alloc(total);
-  b.inv.alloc(total);
+  b.lu.alloc(std::max<int64_t>(total, 1));
+  b.inv.alloc(std::max<int64_t>(total, 1));
   b.piv.alloc(b.piv_off[nc]);
   b.perm.alloc(b.piv_off[nc]);
   b.d_elem_off.alloc(nc + 1);
@@ -509,7 +526,7 @@ void bd_setup(Geom& g) {
   }
   for (int k = 0; k < nc; ++k) {
     const int64_t m = b.rows[k];
-    if (m <= kSmall) continue;
+    if (m <= kSmall) continue;  // (also the skipped wall, m = 0)
     double* A = b.lu.get() + b.elem_off[k];
     int* P = b.piv.get() + b.piv_off[k];
     for (int64_t k0 = 0; k0 < m; k0 += kNb) {
@@ -550,17 +567,19 @@ void bd_setup(Geom& g) {
   STOKES_CUDA(cudaMemcpyAsync(b.perm.get(), hperm.data(), 4 * hperm.size(), cudaMemcpyHostToDevice, s));
   for (int k = 0; k < nc; ++k) {
     const int64_t m = b.rows[k];
-    if (m <= kSmall || m > kInv) continue;
+    if (m <= kSmall || m > kInv) continue;  // m = 0 for a skipped wall
     k_inv_from_lu<<<(unsigned)((m + kInvCols - 1) / kInvCols), 256, 0, s>>>(
         b.lu.get() + b.elem_off[k], m, b.perm.get() + b.piv_off[k], b.inv.get() + b.elem_off[k]);
     STOKES_LAUNCHED();
   }
   // single-precision copies: all inverses, and the factors of the blocks
   // applied by triangular solves
-  b.inv32.alloc(total);
-  k_to_f32<<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32), 256, 0, s>>>(b.inv.get(), b.inv32.get(),
-                                                                                     total);
-  STOKES_LAUNCHED();
+  b.inv32.alloc(std::max<int64_t>(total, 1));
+  if (total > 0) {
+    k_to_f32<<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32), 256, 0, s>>>(b.inv.get(), b.inv32.get(),
+                                                                                       total);
+    STOKES_LAUNCHED();
+  }
   b.lu32_off.assign(nc, -1);
   int64_t tri_total = 0, tri_max = 0;
   for (int k : b.tri_ids) {
@@ -623,6 +642,22 @@ void bd_apply(Geom& g, const double* v, double* z, const int* done, bool f32) {
     }
   }
   g.prof.end(pb, s);
+}
+
+// z += B^-1 h over the blocks that have explicit inverses (the pores, when
+// the wall block was left out).
+void bd_apply_pores_accumulate(Geom& g, const double* h, double* z, const int* done, bool f32) {
+  BlockDiag& b = g.bd;
+  if (b.inv_ids.empty()) return;
+  dim3 grid((unsigned)b.inv_ids.size(), (unsigned)((b.max_inv_rows + 63) / 64));
+  const size_t sm = b.max_inv_rows * (f32 ? sizeof(float) : sizeof(double));
+  if (f32)
+    k_bd_gemv<float, true><<<grid, 256, sm, g.stream>>>(b.d_inv_ids.get(), b.d_rows.get(), b.d_elem_off.get(),
+                                                       b.d_node_off.get(), b.inv32.get(), h, z, done);
+  else
+    k_bd_gemv<double, true><<<grid, 256, sm, g.stream>>>(b.d_inv_ids.get(), b.d_rows.get(), b.d_elem_off.get(),
+                                                        b.d_node_off.get(), b.inv.get(), h, z, done);
+  STOKES_LAUNCHED();
 }
 
 }  // namespace stokes

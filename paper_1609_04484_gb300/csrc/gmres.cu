@@ -280,6 +280,7 @@ static void krylov_alloc(Geom& g, int m) {
     k.sn.alloc(m);
     k.g.alloc(m + 1);
     k.y.alloc(2 * (size_t)(m + 1));  // projection coefficients / y, then back-substitution work
+    k.Zb.release();
     k.m = m;
     k.n2 = n;
   }
@@ -317,8 +318,9 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
   require(restart >= 1 && restart <= kMaxRestart, "restart must be in [1, 8192]");
   require(max_iter >= 1, "max_iter must be >= 1");
   require(tol > 0 && std::isfinite(tol), "tol must be > 0");
-  const bool use_pc = g.bd.ready;
+  const bool use_pc = g.bd.ready || g.tg.ready;
   const bool left = side == STOKES_PC_LEFT && use_pc;
+  require(!(left && g.tg.ready), "the two-grid preconditioner is applied from the right only");
   cudaStream_t s = g.stream;
   const int64_t n = 2 * g.N;
   const int m = restart;
@@ -326,6 +328,8 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
   const int nblk = (int)((n + kChunk - 1) / kChunk);
   const int ldp = m + 1;
   krylov_alloc(g, m);
+  const bool use_pc_any = g.bd.ready || g.tg.ready;
+  if (use_pc_any && side != STOKES_PC_LEFT) k.Zb.alloc((size_t)m * n);
   double* normpart = k.partial.get();  // reductions of norms share the partial buffer
   DevBuf<double> np2;                  // separate buffer for the norm partials inside a step
   np2.alloc(nblk);
@@ -341,7 +345,7 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
   }
   double rhsnorm = fnorm;
   if (left) {
-    bd_apply(g, f, k.t.get(), nullptr, bd32);
+    precond_apply(g, f, k.t.get(), nullptr, bd32);
     rhsnorm = device_norm(g, k.t.get(), n);
   }
   const double xnorm0 = device_norm(g, x, n);
@@ -363,7 +367,7 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
     res.relres = rn / fnorm;
     double beta = rn;
     if (left) {
-      bd_apply(g, k.r.get(), k.Z.get(), nullptr, bd32);
+      precond_apply(g, k.r.get(), k.Z.get(), nullptr, bd32);
       k_copy<<<gv, 256, 0, s>>>(k.r.get(), k.Z.get(), n);
       beta = device_norm(g, k.r.get(), n);
     }
@@ -393,11 +397,13 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
       if (!use_pc) {
         apply_operator(g, vj, k.w.get(), precision, state);
       } else if (!left) {
-        bd_apply(g, vj, k.Z.get(), state, bd32);
-        apply_operator(g, k.Z.get(), k.w.get(), precision, state);
+        // flexible GMRES: keep z_j = P^-1 v_j, the iterate is x0 + Z y
+        double* zj = k.Zb.get() + (int64_t)j * n;
+        precond_apply(g, vj, zj, state, bd32);
+        apply_operator(g, zj, k.w.get(), precision, state);
       } else {
         apply_operator(g, vj, k.t.get(), precision, state);
-        bd_apply(g, k.t.get(), k.w.get(), state, bd32);
+        precond_apply(g, k.t.get(), k.w.get(), state, bd32);
       }
       const int pa = g.prof.begin(kProfArnoldi, 8.0 * n * (4.0 * (j + 1) + 4.0), s);
       for (int pass = 0; pass < 2; ++pass) {
@@ -426,13 +432,8 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
     int hstate[3] = {0, 0, 0};
     STOKES_CUDA(cudaMemcpyAsync(hstate, state, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
     k_lsq_solve<<<1, 256, 0, s>>>(k.H.get(), m, k.g.get(), state, k.y.get(), k.y.get() + (m + 1));
-    k_combine<<<gv, 256, 0, s>>>(k.V.get(), n, k.y.get(), state, k.t.get(), n);
-    if (use_pc && !left) {
-      bd_apply(g, k.t.get(), k.Z.get(), nullptr, bd32);
-      k_axpy<<<gv, 256, 0, s>>>(x, k.Z.get(), n);
-    } else {
-      k_axpy<<<gv, 256, 0, s>>>(x, k.t.get(), n);
-    }
+    k_combine<<<gv, 256, 0, s>>>((use_pc && !left) ? k.Zb.get() : k.V.get(), n, k.y.get(), state, k.t.get(), n);
+    k_axpy<<<gv, 256, 0, s>>>(x, k.t.get(), n);
     STOKES_LAUNCHED();
     STOKES_CUDA(cudaStreamSynchronize(s));
     bd_check_barrier(g);

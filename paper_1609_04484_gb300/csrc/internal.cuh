@@ -108,7 +108,7 @@ struct BlockDiag {
 struct Krylov {
   int m = 0;          // restart length the buffers are sized for
   int64_t n2 = 0;     // vector length 2N
-  DevBuf<double> V, Z, w, t, x, f, r, partial, H, cs, sn, g, y, scal;
+  DevBuf<double> V, Z, Zb, w, t, x, f, r, partial, H, cs, sn, g, y, scal;
   DevBuf<int> state;  // [0] done, [1] columns completed, [2] breakdown
   int nblk = 0;
 };
@@ -157,6 +157,27 @@ struct Prof {
   }
 };
 
+// Two-grid preconditioner: an exact solve with the operator on every q-th
+// node (dense float LU) plus the pores' diagonal blocks on the remainder.
+struct TwoGrid {
+  bool ready = false;
+  int q = 0;
+  int64_t Nc = 0;
+  std::vector<int64_t> off_c;      // coarse component offsets
+  DevBuf<int64_t> d_off_c;
+  DevBuf<int64_t> d_ioff;          // per component: offset of its interpolation matrix
+  DevBuf<float> interp;            // row-major n_f x n_c matrices
+  DevBuf<double2> pos_c, nrm_c;
+  DevBuf<double> w_c;
+  DevBuf<double4_32a> selfc_c;
+  DevBuf<int> comp_c;
+  DevBuf<float> lu;                // 2Nc x 2Nc, column-major, LU in place
+  DevBuf<int> piv, perm, status;
+  DevBuf<double> rc, zc, h;
+  DevBuf<float> work32;
+  DevBuf<int> d_pore_ids;
+};
+
 struct Geom {
   int64_t N = 0;
   int n_comp = 0;
@@ -196,6 +217,7 @@ struct Geom {
   DevBuf<double2> tmp2;
 
   BlockDiag bd;
+  TwoGrid tg;
   Krylov kr;
   Prof prof;
 };
@@ -208,6 +230,7 @@ unsigned long long launches_dlp_df64();
 unsigned long long launches_bd();
 unsigned long long launches_bd_trsv();
 unsigned long long launches_bd_inv32();
+unsigned long long launches_twogrid();
 unsigned long long launches_gmres();
 
 // ---- geometry.cu ----
@@ -230,6 +253,10 @@ void bd_setup(Geom& g);
 // f32: use the single-precision inverses and factors (inner solves)
 void bd_apply(Geom& g, const double* v, double* z, const int* done, bool f32 = false);
 void bd_check_barrier(Geom& g);
+// ---- twogrid.cu ----
+void twogrid_setup(Geom& g, int q);
+// z = P^-1 v with the current preconditioner (two-grid if set up, else block diagonal)
+void precond_apply(Geom& g, const double* v, double* z, const int* done, bool f32);
 void invert_from_lu32(Geom& g, const float* LU, int64_t m, const int* perm, float* X);
 template <class T>
 void lu_solve_persistent(Geom& g, const T* A, int64_t m, const int* perm, const double* v, double* z, T* work,

@@ -1,0 +1,492 @@
+// Two-grid preconditioner (not in the paper: a GPU-native alternative to its
+// block-diagonal baseline).
+//
+//   P^-1 r = I Ac^-1 R r + B^-1 (r - I R r)
+//
+// Ac is the same completed double-layer operator on the coarse grid made of
+// every q-th node of every component (weights times q: the trapezoid rule
+// on the q-times coarser equispaced parameter grid), assembled densely and
+// LU-factorised with partial pivoting in single precision. I interpolates
+// each component's coarse samples trigonometrically (the real interpolant,
+// Nyquist cosine split evenly), R = (n_c / n_f) I^T. B^-1 is the pores'
+// diagonal blocks; on the wall the remainder is multiplied by -2, the inverse
+// of the -1/2 jump (the wall block is not needed next to the coarse solve).
+// The coarse solve rounds its input to float, so the solver runs flexible
+// GMRES, which tolerates a preconditioner that is not exactly linear.
+#include <algorithm>
+#include <cmath>
+#include <map>
+
+#include "internal.cuh"
+
+namespace stokes {
+
+void bd_setup_pores(Geom& g, bool skip_wall);
+void bd_apply_pores_accumulate(Geom& g, const double* h, double* z, const int* done, bool f32);
+
+namespace {
+
+constexpr int kNb = 64;
+
+__global__ void k_coarse_gather(int64_t Nc, int q, const int64_t* __restrict__ off, const int64_t* __restrict__ off_c,
+                                int n_comp, const double2* __restrict__ pos, const double2* __restrict__ nrm,
+                                const double* __restrict__ w, const double4_32a* __restrict__ selfc,
+                                double2* __restrict__ pos_c, double2* __restrict__ nrm_c, double* __restrict__ w_c,
+                                double4_32a* __restrict__ selfc_c, int* __restrict__ comp_c) {
+  count_launch();
+  const int64_t ic = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (ic >= Nc) return;
+  int lo = 0, hi = n_comp - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off_c[mid] <= ic) lo = mid; else hi = mid - 1;
+  }
+  const int k = lo;
+  const int64_t i = off[k] + (int64_t)q * (ic - off_c[k]);
+  pos_c[ic] = pos[i];
+  nrm_c[ic] = nrm[i];
+  w_c[ic] = q * w[i];
+  const double4_32a sc = selfc[i];
+  selfc_c[ic] = make_double4_32a(sc.x, sc.y, q * sc.z, q * sc.w);
+  comp_c[ic] = k;
+}
+
+// Dense coarse operator (column-major, leading dimension 2 Nc), one thread
+// per (row node i, column node j) writing the 2 x 2 block A_ij in float.
+__global__ void __launch_bounds__(256)
+k_coarse_assemble(int64_t Nc, const double2* __restrict__ pos, const double2* __restrict__ nrm,
+                  const double* __restrict__ w, const double4_32a* __restrict__ selfc, const int* __restrict__ comp,
+                  const double2* __restrict__ centre, int outer, float* __restrict__ A) {
+  count_launch();
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= Nc) return;
+  const int64_t ld = 2 * Nc;
+  const double2 xi = pos[i];
+  const int ci = comp[i];
+  for (int64_t j = blockIdx.y; j < Nc; j += gridDim.y) {
+    const int cj = comp[j];
+    const double wj = w[j];
+    double b00, b01, b10, b11;
+    if (i == j) {
+      const double4_32a sc = selfc[i];
+      b00 = sc.z * sc.x * sc.x - 0.5;
+      b01 = sc.z * sc.x * sc.y;
+      b10 = b01;
+      b11 = sc.z * sc.y * sc.y - 0.5;
+    } else {
+      const double2 xj = pos[j];
+      const double2 nj = nrm[j];
+      const double rx = xi.x - xj.x, ry = xi.y - xj.y;
+      const double r2 = rx * rx + ry * ry;
+      const double c = wj * kInvPi * (rx * nj.x + ry * nj.y) / (r2 * r2);
+      b00 = c * rx * rx;
+      b01 = c * rx * ry;
+      b10 = b01;
+      b11 = c * ry * ry;
+    }
+    if (cj != outer) {
+      const double2 c = centre[cj];
+      const double rx = xi.x - c.x, ry = xi.y - c.y;
+      const double r2 = rx * rx + ry * ry;
+      const double lg = -0.5 * log(r2);
+      const double2 xj = pos[j];
+      const double px = (xj.y - c.y) * wj, py = -(xj.x - c.x) * wj;  // w_j (x_j - c)^perp
+      const double ra = ry / r2, rb = -rx / r2;                       // r^perp / rho^2
+      b00 += kInv4Pi * (wj * (lg + rx * rx / r2) + ra * px);
+      b01 += kInv4Pi * (wj * (rx * ry / r2) + ra * py);
+      b10 += kInv4Pi * (wj * (rx * ry / r2) + rb * px);
+      b11 += kInv4Pi * (wj * (lg + ry * ry / r2) + rb * py);
+    } else if (ci == outer) {
+      const double2 ni = nrm[i];
+      const double2 nj = nrm[j];
+      b00 += ni.x * wj * nj.x;
+      b01 += ni.x * wj * nj.y;
+      b10 += ni.y * wj * nj.x;
+      b11 += ni.y * wj * nj.y;
+    }
+    float* col0 = A + (2 * j) * ld + 2 * i;
+    float* col1 = col0 + ld;
+    col0[0] = (float)b00;
+    col0[1] = (float)b10;
+    col1[0] = (float)b01;
+    col1[1] = (float)b11;
+  }
+}
+
+// ---- float blocked LU (right-looking, partial pivoting) ----
+__device__ void argmax_reduce_f(float& v, int64_t& ix) {
+  __shared__ float sv[32];
+  __shared__ int64_t si[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ov = __shfl_down_sync(0xffffffffu, v, o);
+    const int64_t oi = __shfl_down_sync(0xffffffffu, ix, o);
+    if (ov > v || (ov == v && oi < ix)) { v = ov; ix = oi; }
+  }
+  if (lane == 0) { sv[wid] = v; si[wid] = ix; }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    v = lane < nw ? sv[lane] : -1.f;
+    ix = lane < nw ? si[lane] : INT64_MAX;
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ov = __shfl_down_sync(0xffffffffu, v, o);
+      const int64_t oi = __shfl_down_sync(0xffffffffu, ix, o);
+      if (ov > v || (ov == v && oi < ix)) { v = ov; ix = oi; }
+    }
+    if (lane == 0) { sv[0] = v; si[0] = ix; }
+  }
+  __syncthreads();
+  v = sv[0];
+  ix = si[0];
+  __syncthreads();
+}
+
+__global__ void k_piv_partial32(const float* __restrict__ A, int64_t m, int64_t c, float* __restrict__ pv,
+                                int64_t* __restrict__ pi) {
+  count_launch();
+  float best = -1.f;
+  int64_t bi = INT64_MAX;
+  for (int64_t r = c + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x) {
+    const float v = fabsf(A[c * m + r]);
+    if (v > best) { best = v; bi = r; }
+  }
+  argmax_reduce_f(best, bi);
+  if (threadIdx.x == 0) {
+    pv[blockIdx.x] = best;
+    pi[blockIdx.x] = bi;
+    pv[256 + blockIdx.x] = bi < m ? A[c * m + bi] : 0.f;
+  }
+}
+
+__global__ void k_piv_swap32(float* __restrict__ A, int64_t m, int64_t c, int nparts, const float* __restrict__ pv,
+                             const int64_t* __restrict__ pi, int* __restrict__ piv, int* __restrict__ status,
+                             float* __restrict__ inv_out) {
+  count_launch();
+  __shared__ int64_t s_p;
+  if (threadIdx.x == 0) {
+    float best = -1.f, d = 0.f;
+    int64_t bi = INT64_MAX;
+    for (int b = 0; b < nparts; ++b)
+      if (pv[b] > best || (pv[b] == best && pi[b] < bi)) { best = pv[b]; bi = pi[b]; d = pv[256 + b]; }
+    if (bi >= m) { bi = c; d = 0.f; }
+    s_p = bi;
+    if (blockIdx.x == 0) {
+      piv[c] = (int)bi;
+      if (d == 0.f || !isfinite(d)) { atomicExch(status, 1); *inv_out = 0.f; } else *inv_out = 1.f / d;
+    }
+  }
+  __syncthreads();
+  const int64_t p = s_p;
+  if (p != c)
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < m; q += (int64_t)gridDim.x * blockDim.x) {
+      const float t = A[q * m + c];
+      A[q * m + c] = A[q * m + p];
+      A[q * m + p] = t;
+    }
+}
+
+__global__ void k_panel_update32(float* __restrict__ A, int64_t m, int64_t c, int64_t pend,
+                                 const float* __restrict__ inv_ptr) {
+  count_launch();
+  const float iv = *inv_ptr;
+  for (int64_t r = c + 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const float l = A[c * m + r] * iv;
+    A[c * m + r] = l;
+    for (int64_t q = c + 1; q < pend; ++q) A[q * m + r] -= l * A[q * m + c];
+  }
+}
+
+__global__ void k_trsm_row_panel32(float* __restrict__ A, int64_t m, int64_t k0, int kb) {
+  count_launch();
+  const int64_t q = k0 + kb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= m) return;
+  float* col = A + q * m + k0;
+  float x[kNb];
+#pragma unroll
+  for (int c = 0; c < kNb; ++c) x[c] = c < kb ? col[c] : 0.f;
+#pragma unroll
+  for (int c = 0; c < kNb; ++c) {
+    if (c >= kb) break;
+    const float xc = x[c];
+#pragma unroll
+    for (int r = c + 1; r < kNb; ++r)
+      if (r < kb) x[r] -= A[(k0 + c) * m + k0 + r] * xc;
+  }
+#pragma unroll
+  for (int c = 0; c < kNb; ++c)
+    if (c < kb) col[c] = x[c];
+}
+
+// trailing update A22 -= L21 U12: 128 x 128 output tile per CTA, 8 x 8 per
+// thread, operands staged 16 columns / rows at a time.
+__global__ void __launch_bounds__(256)
+k_gemm_trailing32(float* __restrict__ A, int64_t m, int64_t k0, int kb) {
+  count_launch();
+  constexpr int kK = 16, kT = 128;
+  __shared__ float sL[kK][kT + 4];
+  __shared__ float sU[kK][kT + 4];
+  const int64_t base = k0 + kb;
+  const int64_t r0 = base + blockIdx.x * (int64_t)kT, q0 = base + blockIdx.y * (int64_t)kT;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[8][8] = {};
+  for (int cb = 0; cb < kb; cb += kK) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < kK * kT; e += 256) {
+      const int c = e / kT, rr = e % kT;
+      const int64_t r = r0 + rr;
+      sL[c][rr] = (cb + c < kb && r < m) ? A[(k0 + cb + c) * m + r] : 0.f;
+    }
+    for (int e = threadIdx.x; e < kK * kT; e += 256) {
+      const int qq = e / kK, c = e % kK;
+      const int64_t q = q0 + qq;
+      sU[c][qq] = (cb + c < kb && q < m) ? A[q * m + k0 + cb + c] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < kK; ++c) {
+      float l[8], u[8];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        l[a] = sL[c][tx + 16 * a];
+        u[a] = sU[c][ty + 16 * a];
+      }
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(l[a], u[b], acc[a][b]);
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const int64_t q = q0 + ty + 16 * b;
+    if (q >= m) continue;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int64_t r = r0 + tx + 16 * a;
+      if (r < m) A[q * m + r] -= acc[a][b];
+    }
+  }
+}
+
+// rc = R r per component (x and y): rc_j = (n_c / n_f) sum_i P[i][j] r_i.
+// Transfers run in single precision (a preconditioner: flexible GMRES
+// absorbs the rounding).
+__global__ void k_restrict(int n_comp, const int64_t* __restrict__ off, const int64_t* __restrict__ off_c,
+                           const int64_t* __restrict__ ioff, const float* __restrict__ P, const double* __restrict__ r,
+                           double* __restrict__ rc, const int* __restrict__ done) {
+  count_launch();
+  if (done && *done) return;
+  const int k = blockIdx.y;
+  const int64_t nf = off[k + 1] - off[k], nc = off_c[k + 1] - off_c[k];
+  const float* Pk = P + ioff[k];
+  const double2* rk = reinterpret_cast<const double2*>(r) + off[k];
+  const float scale = (float)nc / (float)nf;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nc; j += (int64_t)gridDim.x * blockDim.x) {
+    float ax = 0.f, ay = 0.f;
+    for (int64_t i = 0; i < nf; ++i) {
+      const float p = Pk[i * nc + j];
+      const double2 v = rk[i];
+      ax = fmaf(p, (float)v.x, ax);
+      ay = fmaf(p, (float)v.y, ay);
+    }
+    rc[2 * (off_c[k] + j)] = (double)(scale * ax);
+    rc[2 * (off_c[k] + j) + 1] = (double)(scale * ay);
+  }
+}
+
+// z = I zc (+ -2 h on the wall), h = r - I rc
+__global__ void k_prolong(int n_comp, int outer, const int64_t* __restrict__ off, const int64_t* __restrict__ off_c,
+                          const int64_t* __restrict__ ioff, const float* __restrict__ P, const double* __restrict__ r,
+                          const double* __restrict__ rc, const double* __restrict__ zc, double* __restrict__ z,
+                          double* __restrict__ h, const int* __restrict__ done) {
+  count_launch();
+  if (done && *done) return;
+  const int k = blockIdx.y;
+  const int64_t nf = off[k + 1] - off[k], nc = off_c[k + 1] - off_c[k];
+  const float* Pk = P + ioff[k];
+  const double2* rck = reinterpret_cast<const double2*>(rc) + off_c[k];
+  const double2* zck = reinterpret_cast<const double2*>(zc) + off_c[k];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nf; i += (int64_t)gridDim.x * blockDim.x) {
+    float ux = 0.f, uy = 0.f, vx = 0.f, vy = 0.f;
+    const float* row = Pk + i * nc;
+    for (int64_t j = 0; j < nc; ++j) {
+      const float p = row[j];
+      const double2 zv = zck[j], rv = rck[j];
+      ux = fmaf(p, (float)zv.x, ux);
+      uy = fmaf(p, (float)zv.y, uy);
+      vx = fmaf(p, (float)rv.x, vx);
+      vy = fmaf(p, (float)rv.y, vy);
+    }
+    const int64_t o = 2 * (off[k] + i);
+    const double hx = r[o] - vx, hy = r[o + 1] - vy;
+    h[o] = hx;
+    h[o + 1] = hy;
+    if (k == outer) {
+      z[o] = ux - 2.0 * hx;
+      z[o + 1] = uy - 2.0 * hy;
+    } else {
+      z[o] = ux;
+      z[o + 1] = uy;
+    }
+  }
+}
+
+// Real trigonometric interpolation matrix nf x nc (row-major), see the top.
+std::vector<float> trig_interp(int64_t nc, int64_t nf) {
+  std::vector<float> P((size_t)(nf * nc));
+  const int64_t K = (nc + 1) / 2 - 1;
+  for (int64_t i = 0; i < nf; ++i)
+    for (int64_t j = 0; j < nc; ++j) {
+      const double d = 2.0 * kPi * (double)i / (double)nf - 2.0 * kPi * (double)j / (double)nc;
+      double v = 1.0;
+      for (int64_t k = 1; k <= K; ++k) v += 2.0 * std::cos((double)k * d);
+      if (nc % 2 == 0) v += std::cos((double)(nc / 2) * d);
+      P[(size_t)(i * nc + j)] = (float)(v / (double)nc);
+    }
+  return P;
+}
+
+}  // namespace
+
+void twogrid_setup(Geom& g, int q) {
+  TwoGrid& t = g.tg;
+  t.ready = false;
+  require(q >= 2, "coarsening factor must be >= 2");
+  const int nc = g.n_comp;
+  cudaStream_t s = g.stream;
+  t.q = q;
+  t.off_c.assign(nc + 1, 0);
+  for (int k = 0; k < nc; ++k) {
+    const int64_t n = g.off[k + 1] - g.off[k];
+    require(n % q == 0 && n / q >= 8, "two-grid: every component needs a multiple of q nodes, at least 8 q");
+    t.off_c[k + 1] = t.off_c[k] + n / q;
+  }
+  const int64_t Nc = t.off_c[nc];
+  t.Nc = Nc;
+  const int64_t m = 2 * Nc;
+  require((double)m * (double)m * 4.0 < 64e9, "two-grid: coarse operator too large (reduce with a larger q)");
+  // interpolation matrices, one per distinct (n_f, n_c)
+  std::map<std::pair<int64_t, int64_t>, int64_t> seen;
+  std::vector<float> pool;
+  std::vector<int64_t> ioff(nc);
+  for (int k = 0; k < nc; ++k) {
+    const int64_t nf = g.off[k + 1] - g.off[k], ncc = nf / q;
+    auto key = std::make_pair(nf, ncc);
+    auto it = seen.find(key);
+    if (it == seen.end()) {
+      const std::vector<float> P = trig_interp(ncc, nf);
+      seen[key] = (int64_t)pool.size();
+      ioff[k] = (int64_t)pool.size();
+      pool.insert(pool.end(), P.begin(), P.end());
+    } else {
+      ioff[k] = it->second;
+    }
+  }
+  t.interp.alloc(pool.size());
+  t.d_ioff.alloc(nc);
+  t.d_off_c.alloc(nc + 1);
+  STOKES_CUDA(cudaMemcpyAsync(t.interp.get(), pool.data(), 4 * pool.size(), cudaMemcpyHostToDevice, s));
+  STOKES_CUDA(cudaMemcpyAsync(t.d_ioff.get(), ioff.data(), 8 * nc, cudaMemcpyHostToDevice, s));
+  STOKES_CUDA(cudaMemcpyAsync(t.d_off_c.get(), t.off_c.data(), 8 * (nc + 1), cudaMemcpyHostToDevice, s));
+  // coarse nodes
+  t.pos_c.alloc(Nc);
+  t.nrm_c.alloc(Nc);
+  t.w_c.alloc(Nc);
+  t.selfc_c.alloc(Nc);
+  t.comp_c.alloc(Nc);
+  k_coarse_gather<<<(unsigned)((Nc + 255) / 256), 256, 0, s>>>(Nc, q, g.d_off.get(), t.d_off_c.get(), nc, g.pos.get(),
+                                                              g.nrm.get(), g.w.get(), g.selfc.get(), t.pos_c.get(),
+                                                              t.nrm_c.get(), t.w_c.get(), t.selfc_c.get(),
+                                                              t.comp_c.get());
+  STOKES_LAUNCHED();
+  const int ps = g.prof.begin(kProfBdSetup, (2.0 / 3.0) * (double)m * m * m, s);
+  // assemble and factorise the coarse operator
+  t.lu.alloc((size_t)m * m);
+  dim3 ga((unsigned)((Nc + 255) / 256), (unsigned)std::min<int64_t>(Nc, 16384));
+  k_coarse_assemble<<<ga, 256, 0, s>>>(Nc, t.pos_c.get(), t.nrm_c.get(), t.w_c.get(), t.selfc_c.get(), t.comp_c.get(),
+                                       g.centre.get(), g.outer, t.lu.get());
+  STOKES_LAUNCHED();
+  t.piv.alloc(m);
+  t.status.alloc(1);
+  STOKES_CUDA(cudaMemsetAsync(t.status.get(), 0, sizeof(int), s));
+  DevBuf<float> pv, ivp;
+  DevBuf<int64_t> pi;
+  pv.alloc(512);
+  pi.alloc(256);
+  ivp.alloc(1);
+  float* A = t.lu.get();
+  for (int64_t k0 = 0; k0 < m; k0 += kNb) {
+    const int kb = (int)std::min<int64_t>(kNb, m - k0);
+    for (int64_t c = k0; c < k0 + kb; ++c) {
+      const int parts = (int)std::min<int64_t>(256, (m - c + 255) / 256);
+      k_piv_partial32<<<parts, 256, 0, s>>>(A, m, c, pv.get(), pi.get());
+      k_piv_swap32<<<(unsigned)std::min<int64_t>(64, (m + 255) / 256), 256, 0, s>>>(A, m, c, parts, pv.get(), pi.get(),
+                                                                                   t.piv.get(), t.status.get(),
+                                                                                   ivp.get());
+      const int64_t nr = m - c - 1;
+      if (nr > 0)
+        k_panel_update32<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(1024, (nr + 127) / 128)), 128, 0, s>>>(
+            A, m, c, k0 + kb, ivp.get());
+    }
+    const int64_t rest = m - k0 - kb;
+    if (rest > 0) {
+      k_trsm_row_panel32<<<(unsigned)((rest + 127) / 128), 128, 0, s>>>(A, m, k0, kb);
+      dim3 grid((unsigned)((rest + 127) / 128), (unsigned)((rest + 127) / 128));
+      k_gemm_trailing32<<<grid, 256, 0, s>>>(A, m, k0, kb);
+    }
+    STOKES_LAUNCHED();
+  }
+  std::vector<int> hpiv(m);
+  int hstatus = 0;
+  STOKES_CUDA(cudaMemcpyAsync(hpiv.data(), t.piv.get(), 4 * m, cudaMemcpyDeviceToHost, s));
+  STOKES_CUDA(cudaMemcpyAsync(&hstatus, t.status.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+  STOKES_CUDA(cudaStreamSynchronize(s));
+  require(hstatus == 0, "two-grid: singular coarse operator (zero pivot)", STOKES_EBREAKDOWN);
+  std::vector<int> perm(m);
+  for (int64_t r = 0; r < m; ++r) perm[r] = (int)r;
+  for (int64_t c = 0; c < m; ++c) std::swap(perm[c], perm[hpiv[c]]);
+  t.perm.alloc(m);
+  STOKES_CUDA(cudaMemcpyAsync(t.perm.get(), perm.data(), 4 * m, cudaMemcpyHostToDevice, s));
+  t.rc.alloc(m);
+  t.zc.alloc(m);
+  t.h.alloc(2 * g.N);
+  t.work32.alloc(m);
+  g.prof.end(ps, s);
+  // fine blocks of the pores (the wall block is replaced by -2 I)
+  bd_setup_pores(g, /*skip_wall=*/true);
+  STOKES_CUDA(cudaStreamSynchronize(s));
+  t.ready = true;
+}
+
+static void twogrid_apply(Geom& g, const double* r, double* z, const int* done, bool f32) {
+  TwoGrid& t = g.tg;
+  cudaStream_t s = g.stream;
+  const int nc = g.n_comp;
+  const int64_t nmax = std::max<int64_t>(1, (g.N + 255) / 256);
+  dim3 gr((unsigned)std::min<int64_t>(16, nmax), (unsigned)nc);
+  k_restrict<<<gr, 128, 0, s>>>(nc, g.d_off.get(), t.d_off_c.get(), t.d_ioff.get(), t.interp.get(), r, t.rc.get(),
+                                done);
+  STOKES_LAUNCHED();
+  lu_solve_persistent<float>(g, t.lu.get(), 2 * t.Nc, t.perm.get(), t.rc.get(), t.zc.get(), t.work32.get(), done);
+  dim3 gp((unsigned)std::min<int64_t>(64, nmax), (unsigned)nc);
+  k_prolong<<<gp, 128, 0, s>>>(nc, g.outer, g.d_off.get(), t.d_off_c.get(), t.d_ioff.get(), t.interp.get(), r,
+                               t.rc.get(), t.zc.get(), z, t.h.get(), done);
+  STOKES_LAUNCHED();
+  bd_apply_pores_accumulate(g, t.h.get(), z, done, f32);
+}
+
+void precond_apply(Geom& g, const double* v, double* z, const int* done, bool f32) {
+  if (g.tg.ready) {
+    const int pb = g.prof.begin(kProfBdApply, 0.0, g.stream);
+    twogrid_apply(g, v, z, done, f32);
+    g.prof.end(pb, g.stream);
+  } else {
+    bd_apply(g, v, z, done, f32);
+  }
+}
+
+unsigned long long launches_twogrid() { return tu_launches(); }
+
+}  // namespace stokes

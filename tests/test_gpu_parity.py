@@ -348,3 +348,47 @@ def test_unrestarted_gmres_long_basis(S, dev):
         code, iters, rr, _ = S.stokes_gmres_solve(G.handle, f, sig, tol=1e-11, restart=1500, max_iter=1500)
         assert code == S.STOKES_OK and rr <= 1e-11 and iters < 1500
         assert rel(sig, ref) < 1e-9
+
+
+@pytest.mark.parametrize("prec", ["FP64", "DF64", "MIXED_IR"])
+def test_two_grid_solve_matches_dense_oracle(S, dev, prec):
+    """Flexible GMRES with the two-grid preconditioner reaches the dense FP64
+    solution, in about as many iterations as the oracle's two-grid FGMRES
+    (whose coarse LU is double: the float one here may cost a few more)."""
+    g = si.config1_geometry(0, n_outer=256, n_pores=6, n_per_pore=32)
+    f = si.pipe_bc(g).reshape(-1)
+    A = O.assemble(g)
+    ref = np.linalg.solve(A, f)
+    r_or = O.fgmres(lambda v: A @ v, f, O.TwoGrid(g, 4).apply, tol=1e-11)
+    with S.Geometry(g) as G:
+        S.stokes_precond_setup_twogrid(G.handle, 4)
+        sig = np.zeros_like(f)
+        code, iters, rr, _ = S.stokes_gmres_solve(G.handle, f, sig, tol=1e-11, restart=100,
+                                                  precision=getattr(S, "STOKES_" + prec))
+        assert code == S.STOKES_OK and rr <= 1e-11
+        assert rel(sig, ref) < 1e-9
+        if prec != "MIXED_IR":
+            assert iters <= r_or["iters"] + 3
+
+
+def test_two_grid_apply_matches_oracle(S, dev):
+    """P^-1 v against the oracle's double-precision two-grid apply: equal up
+    to the float coarse factorisation (coarse condition number x 1e-7)."""
+    g = si.config1_geometry(1, n_outer=256, n_pores=5, n_per_pore=32)
+    v = np.random.default_rng(2).standard_normal(2 * g.n_nodes)
+    ref = O.TwoGrid(g, 4).apply(v)
+    with S.Geometry(g) as G:
+        S.stokes_precond_setup_twogrid(G.handle, 4)
+        z = np.empty_like(v)
+        S.stokes_precond_apply(G.handle, v, z)
+        assert rel(z, ref) < 1e-3
+
+
+def test_two_grid_rejects_bad_coarsening(S, dev):
+    g = si.config1_geometry(0, n_outer=96, n_pores=2, n_per_pore=24)
+    with S.Geometry(g) as G:
+        with pytest.raises(S.StokesError) as e:
+            S.stokes_precond_setup_twogrid(G.handle, 5)    # 24 not a multiple of 5
+        assert e.value.code == S.STOKES_EINVAL
+        with pytest.raises(S.StokesError):
+            S.stokes_precond_setup_twogrid(G.handle, 4)    # 24 / 4 = 6 < 8 coarse nodes
