@@ -70,7 +70,7 @@ enum stokes_status {
  * STOKES_DF64: double-float pair sums (unevaluated sums of two floats with
  *   error-free transformations) giving FP64-class accuracy on the FP32 pipes.
  * STOKES_MIXED_IR (solve only): FP32 inner GMRES inside FP64 iterative
- *   refinement; the outer residual uses the DF64 operator. */
+ *   refinement; the outer residual uses the native FP64 operator. */
 enum stokes_precision {
   STOKES_FP64 = 0,
   STOKES_FP32 = 1,
@@ -166,9 +166,11 @@ int stokes_precond_apply_prec(stokes_geom* g, const double* v, double* z, int pr
  *   max_iter total inner iterations (>= 1)
  *   precision STOKES_FP64, STOKES_FP32, STOKES_DF64 (operator arithmetic;
  *             Arnoldi, Givens and the least-squares update always FP64; the
- *             true residual is that of the chosen operator, so FP32 stalls
- *             near single-precision accuracy) or STOKES_MIXED_IR
- *             (iterative refinement: outer residual with the DF64 operator,
+ *             true residual, recomputed at every restart, is that of the
+ *             chosen operator (FP32 stalls near single precision), except
+ *             that DF64 solves take it with the native FP64 operator) or
+ *             STOKES_MIXED_IR
+ *             (iterative refinement: outer residual with the FP64 operator,
  *             corrections by GMRES on the FP32 operator until its Arnoldi
  *             residual estimate is below max(1e-4, tol / (2 |r| / |f|));
  *             STOKES_TRACE=1 in the environment prints each step; iters_out counts the

@@ -356,7 +356,10 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
     if (x_is_zero) {
       k_residual_norm<<<nblk, 256, 0, s>>>(f, nullptr, k.r.get(), n, normpart);
     } else {
-      apply_operator(g, x, k.t.get(), precision, nullptr);
+      // the true residual of the double-float solve is taken with the native
+      // FP64 operator: large densities (ill-conditioned systems) amplify the
+      // double-float operator's ~1e-12 relative error past the tolerance
+      apply_operator(g, x, k.t.get(), (precision == STOKES_DF64 && !inner) ? STOKES_FP64 : precision, nullptr);
       k_residual_norm<<<nblk, 256, 0, s>>>(f, k.t.get(), k.r.get(), n, normpart);
     }
     k_norm_final<<<1, 32, 0, s>>>(normpart, nblk, k.scal.get(), 2);
@@ -467,7 +470,7 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
 namespace stokes {
 
 // Mixed-precision iterative refinement: the outer residual r = f - A x uses
-// the double-float operator (FP64-class); each correction solves A d = r
+// the native FP64 operator; each correction solves A d = r
 // with GMRES on the FP32 operator until its Arnoldi residual estimate drops
 // below max(1e-4, tol / (2 |r| / |f|)) (Arnoldi, Givens and least squares
 // stay FP64), then x += d. STOKES_TRACE=1 prints each refinement step.
@@ -490,7 +493,7 @@ static SolveResult ir_solve(Geom& g, const double* f, double* x, double tol, int
   const unsigned gv = grid_for(n);
   int iters = 0;
   for (int outer = 0;; ++outer) {
-    apply_operator(g, x, t.get(), STOKES_DF64, nullptr);
+    apply_operator(g, x, t.get(), STOKES_FP64, nullptr);
     const int nblk = (int)((n + kChunk - 1) / kChunk);
     k_residual_norm<<<nblk, 256, 0, s>>>(f, t.get(), r.get(), n, g.kr.partial.get());
     k_norm_final<<<1, 32, 0, s>>>(g.kr.partial.get(), nblk, g.kr.scal.get(), 2);

@@ -171,7 +171,8 @@ struct TwoGrid {
   DevBuf<double> w_c;
   DevBuf<double4_32a> selfc_c;
   DevBuf<int> comp_c;
-  DevBuf<float> lu;                // 2Nc x 2Nc, column-major, LU in place
+  DevBuf<float> lu;                // 2Nc x 2Nc, column-major, LU in place (setup only)
+  DevBuf<float> inv;               // its explicit inverse
   DevBuf<int> piv, perm, status;
   DevBuf<double> rc, zc, h;
   DevBuf<float> work32;

@@ -52,7 +52,10 @@ __global__ void k_coarse_gather(int64_t Nc, int q, const int64_t* __restrict__ o
 }
 
 // Dense coarse operator (column-major, leading dimension 2 Nc), one thread
-// per (row node i, column node j) writing the 2 x 2 block A_ij in float.
+// per (row node i, column node j) writing the 2 x 2 block A_ij. The result
+// is stored and factorised in float, so it is evaluated in float too, with
+// differences of positions formed from float hi + lo parts (accurate to
+// float precision relative to the distance).
 __global__ void __launch_bounds__(256)
 k_coarse_assemble(int64_t Nc, const double2* __restrict__ pos, const double2* __restrict__ nrm,
                   const double* __restrict__ w, const double4_32a* __restrict__ selfc, const int* __restrict__ comp,
@@ -61,56 +64,83 @@ k_coarse_assemble(int64_t Nc, const double2* __restrict__ pos, const double2* __
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= Nc) return;
   const int64_t ld = 2 * Nc;
-  const double2 xi = pos[i];
+  const double2 xid = pos[i];
+  const float xh = (float)xid.x, yh = (float)xid.y;
+  const float xl = (float)(xid.x - (double)xh), yl = (float)(xid.y - (double)yh);
   const int ci = comp[i];
+  const double2 nid = nrm[i];
   for (int64_t j = blockIdx.y; j < Nc; j += gridDim.y) {
     const int cj = comp[j];
-    const double wj = w[j];
-    double b00, b01, b10, b11;
+    const float wj = (float)w[j];
+    const double2 xjd = pos[j];
+    const float jxh = (float)xjd.x, jyh = (float)xjd.y;
+    const float jxl = (float)(xjd.x - (double)jxh), jyl = (float)(xjd.y - (double)jyh);
+    float b00, b01, b10, b11;
     if (i == j) {
       const double4_32a sc = selfc[i];
-      b00 = sc.z * sc.x * sc.x - 0.5;
-      b01 = sc.z * sc.x * sc.y;
+      b00 = (float)(sc.z * sc.x * sc.x - 0.5);
+      b01 = (float)(sc.z * sc.x * sc.y);
       b10 = b01;
-      b11 = sc.z * sc.y * sc.y - 0.5;
+      b11 = (float)(sc.z * sc.y * sc.y - 0.5);
     } else {
-      const double2 xj = pos[j];
       const double2 nj = nrm[j];
-      const double rx = xi.x - xj.x, ry = xi.y - xj.y;
-      const double r2 = rx * rx + ry * ry;
-      const double c = wj * kInvPi * (rx * nj.x + ry * nj.y) / (r2 * r2);
+      const float rx = (xh - jxh) + (xl - jxl), ry = (yh - jyh) + (yl - jyl);
+      const float r2 = fmaf(rx, rx, ry * ry);
+      const float inv = __frcp_rn(r2);
+      const float c = wj * (float)kInvPi * fmaf(rx, (float)nj.x, ry * (float)nj.y) * inv * inv;
       b00 = c * rx * rx;
       b01 = c * rx * ry;
       b10 = b01;
       b11 = c * ry * ry;
     }
     if (cj != outer) {
-      const double2 c = centre[cj];
-      const double rx = xi.x - c.x, ry = xi.y - c.y;
-      const double r2 = rx * rx + ry * ry;
-      const double lg = -0.5 * log(r2);
-      const double2 xj = pos[j];
-      const double px = (xj.y - c.y) * wj, py = -(xj.x - c.x) * wj;  // w_j (x_j - c)^perp
-      const double ra = ry / r2, rb = -rx / r2;                       // r^perp / rho^2
-      b00 += kInv4Pi * (wj * (lg + rx * rx / r2) + ra * px);
-      b01 += kInv4Pi * (wj * (rx * ry / r2) + ra * py);
-      b10 += kInv4Pi * (wj * (rx * ry / r2) + rb * px);
-      b11 += kInv4Pi * (wj * (lg + ry * ry / r2) + rb * py);
+      const double2 cc = centre[cj];
+      const float chx = (float)cc.x, chy = (float)cc.y;
+      const float clx = (float)(cc.x - (double)chx), cly = (float)(cc.y - (double)chy);
+      const float rx = (xh - chx) + (xl - clx), ry = (yh - chy) + (yl - cly);
+      const float r2 = fmaf(rx, rx, ry * ry);
+      const float inv = __frcp_rn(r2);
+      const float lg = -0.5f * __logf(r2);
+      const float px = ((jyh - chy) + (jyl - cly)) * wj, py = -((jxh - chx) + (jxl - clx)) * wj;
+      const float ra = ry * inv, rb = -rx * inv;
+      const float k4 = (float)kInv4Pi;
+      b00 += k4 * (wj * (lg + rx * rx * inv) + ra * px);
+      b01 += k4 * (wj * (rx * ry * inv) + ra * py);
+      b10 += k4 * (wj * (rx * ry * inv) + rb * px);
+      b11 += k4 * (wj * (lg + ry * ry * inv) + rb * py);
     } else if (ci == outer) {
-      const double2 ni = nrm[i];
       const double2 nj = nrm[j];
-      b00 += ni.x * wj * nj.x;
-      b01 += ni.x * wj * nj.y;
-      b10 += ni.y * wj * nj.x;
-      b11 += ni.y * wj * nj.y;
+      b00 += (float)(nid.x * nj.x) * wj;
+      b01 += (float)(nid.x * nj.y) * wj;
+      b10 += (float)(nid.y * nj.x) * wj;
+      b11 += (float)(nid.y * nj.y) * wj;
     }
     float* col0 = A + (2 * j) * ld + 2 * i;
     float* col1 = col0 + ld;
-    col0[0] = (float)b00;
-    col0[1] = (float)b10;
-    col1[0] = (float)b01;
-    col1[1] = (float)b11;
+    col0[0] = b00;
+    col0[1] = b10;
+    col1[0] = b01;
+    col1[1] = b11;
   }
+}
+
+// y = X x for a dense column-major float matrix (double vectors): CTA per
+// 64 rows, the 256 threads split the columns in four interleaved phases.
+__global__ void __launch_bounds__(256)
+k_dense_gemv32(const float* __restrict__ X, int64_t m, const double* __restrict__ x, double* __restrict__ y,
+               const int* __restrict__ done) {
+  count_launch();
+  if (done && *done) return;
+  __shared__ float red[4][64];
+  const int64_t r0 = blockIdx.x * (int64_t)64;
+  const int rr = threadIdx.x & 63, ph = threadIdx.x >> 6;
+  const int64_t r = r0 + rr;
+  float acc = 0.f;
+  if (r < m)
+    for (int64_t q = ph; q < m; q += 4) acc = fmaf(X[q * m + r], (float)x[q], acc);
+  red[ph][rr] = acc;
+  __syncthreads();
+  if (ph == 0 && r < m) y[r] = (double)((red[0][rr] + red[1][rr]) + (red[2][rr] + red[3][rr]));
 }
 
 // ---- float blocked LU (right-looking, partial pivoting) ----
@@ -401,7 +431,7 @@ void twogrid_setup(Geom& g, int q) {
                                                               t.nrm_c.get(), t.w_c.get(), t.selfc_c.get(),
                                                               t.comp_c.get());
   STOKES_LAUNCHED();
-  const int ps = g.prof.begin(kProfBdSetup, (2.0 / 3.0) * (double)m * m * m, s);
+  const int ps = g.prof.begin(kProfBdSetup, 2.0 * (double)m * m * m, s);
   // assemble and factorise the coarse operator
   t.lu.alloc((size_t)m * m);
   dim3 ga((unsigned)((Nc + 255) / 256), (unsigned)std::min<int64_t>(Nc, 16384));
@@ -452,7 +482,11 @@ void twogrid_setup(Geom& g, int q) {
   t.rc.alloc(m);
   t.zc.alloc(m);
   t.h.alloc(2 * g.N);
-  t.work32.alloc(m);
+  // explicit float inverse of the coarse operator: each apply is then one
+  // memory-bound matrix-vector product
+  t.inv.alloc((size_t)m * m);
+  invert_from_lu32(g, t.lu.get(), m, t.perm.get(), t.inv.get());
+  t.lu.release();
   g.prof.end(ps, s);
   // fine blocks of the pores (the wall block is replaced by -2 I)
   bd_setup_pores(g, /*skip_wall=*/true);
@@ -469,7 +503,9 @@ static void twogrid_apply(Geom& g, const double* r, double* z, const int* done, 
   k_restrict<<<gr, 128, 0, s>>>(nc, g.d_off.get(), t.d_off_c.get(), t.d_ioff.get(), t.interp.get(), r, t.rc.get(),
                                 done);
   STOKES_LAUNCHED();
-  lu_solve_persistent<float>(g, t.lu.get(), 2 * t.Nc, t.perm.get(), t.rc.get(), t.zc.get(), t.work32.get(), done);
+  const int64_t m = 2 * t.Nc;
+  k_dense_gemv32<<<(unsigned)((m + 63) / 64), 256, 0, s>>>(t.inv.get(), m, t.rc.get(), t.zc.get(), done);
+  STOKES_LAUNCHED();
   dim3 gp((unsigned)std::min<int64_t>(64, nmax), (unsigned)nc);
   k_prolong<<<gp, 128, 0, s>>>(nc, g.outer, g.d_off.get(), t.d_off_c.get(), t.d_ioff.get(), t.interp.get(), r,
                                t.rc.get(), t.zc.get(), z, t.h.get(), done);
