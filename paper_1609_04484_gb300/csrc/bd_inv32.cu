@@ -10,7 +10,7 @@
 //   forward:  W_t = inv(L_tt) B_t,  B_u -= L_ut W_t  (u > t)
 //   backward: X_t = inv(U_tt) W_t,  W_u -= U_ut X_t  (u < t)
 // where the tile inverses come from small one-CTA kernels and the updates
-// are float tiled GEMMs (64 x 64 output tile per CTA, 4 x 4 per thread).
+// are float tiled GEMMs (128 x 128 output tile per CTA, 8 x 8 per thread).
 #include <algorithm>
 
 #include "internal.cuh"
@@ -21,52 +21,51 @@ namespace {
 
 constexpr int kTs = 64;
 
-// C = alpha A B + beta C (column-major, M x N = (M x K)(K x N)).
+// C = alpha A B + beta C (column-major, M x N = (M x K)(K x N)): 128 x 128
+// output tile per CTA, 8 x 8 per thread, operands staged 16 deep.
 __global__ void __launch_bounds__(256)
 k_sgemm(int64_t M, int64_t N, int K, float alpha, const float* __restrict__ A, int64_t lda,
         const float* __restrict__ B, int64_t ldb, float beta, float* __restrict__ C, int64_t ldc) {
   count_launch();
-  constexpr int kK = 16;
-  __shared__ float sA[kK][64 + 4];  // [k][row]
-  __shared__ float sB[kK][64 + 4];  // [k][col]
-  const int64_t r0 = blockIdx.x * (int64_t)64, c0 = blockIdx.y * (int64_t)64;
+  constexpr int kK = 16, kT = 128;
+  __shared__ float sA[kK][kT + 4];  // [k][row]
+  __shared__ float sB[kK][kT + 4];  // [k][col]
+  const int64_t r0 = blockIdx.x * (int64_t)kT, c0 = blockIdx.y * (int64_t)kT;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  float acc[4][4] = {};
+  float acc[8][8] = {};
   for (int k0 = 0; k0 < K; k0 += kK) {
     __syncthreads();
-    for (int e = threadIdx.x; e < kK * 64; e += 256) {
-      const int kk = e / 64, rr = e % 64;
+    for (int e = threadIdx.x; e < kK * kT; e += 256) {
+      const int kk = e / kT, rr = e % kT;
       const int64_t r = r0 + rr;
-      const bool kin = k0 + kk < K;
-      sA[kk][rr] = (kin && r < M) ? A[(int64_t)(k0 + kk) * lda + r] : 0.f;
+      sA[kk][rr] = (k0 + kk < K && r < M) ? A[(int64_t)(k0 + kk) * lda + r] : 0.f;
     }
-    for (int e = threadIdx.x; e < kK * 64; e += 256) {
-      const int cc = e / kK, kk = e % kK;  // consecutive threads walk k: B column-major
+    for (int e = threadIdx.x; e < kK * kT; e += 256) {
+      const int cc = e / kK, kk = e % kK;
       const int64_t c = c0 + cc;
-      const bool kin = k0 + kk < K;
-      sB[kk][cc] = (kin && c < N) ? B[c * ldb + k0 + kk] : 0.f;
+      sB[kk][cc] = (k0 + kk < K && c < N) ? B[c * ldb + k0 + kk] : 0.f;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < kK; ++kk) {
-      float a[4], b[4];
+      float a[8], b[8];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < 8; ++q) {
         a[q] = sA[kk][tx + 16 * q];
         b[q] = sB[kk][ty + 16 * q];
       }
 #pragma unroll
-      for (int p = 0; p < 4; ++p)
+      for (int p = 0; p < 8; ++p)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(a[p], b[q], acc[p][q]);
+        for (int q = 0; q < 8; ++q) acc[p][q] = fmaf(a[p], b[q], acc[p][q]);
     }
   }
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < 8; ++q) {
     const int64_t c = c0 + ty + 16 * q;
     if (c >= N) continue;
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
+    for (int p = 0; p < 8; ++p) {
       const int64_t r = r0 + tx + 16 * p;
       if (r < M) {
         float* cp = C + c * ldc + r;
@@ -135,7 +134,7 @@ __global__ void k_copy_rows(const float* __restrict__ src, int64_t lds, float* _
 void sgemm(cudaStream_t s, int64_t M, int64_t N, int K, float alpha, const float* A, int64_t lda, const float* B,
            int64_t ldb, float beta, float* C, int64_t ldc) {
   if (M <= 0 || N <= 0) return;
-  dim3 grid((unsigned)((M + 63) / 64), (unsigned)((N + 63) / 64));
+  dim3 grid((unsigned)((M + 127) / 128), (unsigned)((N + 127) / 128));
   k_sgemm<<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
   STOKES_LAUNCHED();
 }

@@ -175,6 +175,7 @@ struct TwoGrid {
   DevBuf<float> inv;               // its explicit inverse
   DevBuf<int> piv, perm, status;
   DevBuf<double> rc, zc, h;
+  DevBuf<float> rc32;
   DevBuf<float> work32;
   DevBuf<int> d_pore_ids;
 };

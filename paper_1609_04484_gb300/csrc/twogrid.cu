@@ -15,6 +15,9 @@
 // GMRES, which tolerates a preconditioner that is not exactly linear.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <ctime>
 #include <map>
 
 #include "internal.cuh"
@@ -127,7 +130,7 @@ k_coarse_assemble(int64_t Nc, const double2* __restrict__ pos, const double2* __
 // y = X x for a dense column-major float matrix (double vectors): CTA per
 // 64 rows, the 256 threads split the columns in four interleaved phases.
 __global__ void __launch_bounds__(256)
-k_dense_gemv32(const float* __restrict__ X, int64_t m, const double* __restrict__ x, double* __restrict__ y,
+k_dense_gemv32(const float* __restrict__ X, int64_t m, const float* __restrict__ x, double* __restrict__ y,
                const int* __restrict__ done) {
   count_launch();
   if (done && *done) return;
@@ -137,7 +140,7 @@ k_dense_gemv32(const float* __restrict__ X, int64_t m, const double* __restrict_
   const int64_t r = r0 + rr;
   float acc = 0.f;
   if (r < m)
-    for (int64_t q = ph; q < m; q += 4) acc = fmaf(X[q * m + r], (float)x[q], acc);
+    for (int64_t q = ph; q < m; q += 4) acc = fmaf(X[q * m + r], x[q], acc);
   red[ph][rr] = acc;
   __syncthreads();
   if (ph == 0 && r < m) y[r] = (double)((red[0][rr] + red[1][rr]) + (red[2][rr] + red[3][rr]));
@@ -305,7 +308,7 @@ k_gemm_trailing32(float* __restrict__ A, int64_t m, int64_t k0, int kb) {
 // absorbs the rounding).
 __global__ void k_restrict(int n_comp, const int64_t* __restrict__ off, const int64_t* __restrict__ off_c,
                            const int64_t* __restrict__ ioff, const float* __restrict__ P, const double* __restrict__ r,
-                           double* __restrict__ rc, const int* __restrict__ done) {
+                           double* __restrict__ rc, float* __restrict__ rc32, const int* __restrict__ done) {
   count_launch();
   if (done && *done) return;
   const int k = blockIdx.y;
@@ -323,6 +326,8 @@ __global__ void k_restrict(int n_comp, const int64_t* __restrict__ off, const in
     }
     rc[2 * (off_c[k] + j)] = (double)(scale * ax);
     rc[2 * (off_c[k] + j) + 1] = (double)(scale * ay);
+    rc32[2 * (off_c[k] + j)] = scale * ax;
+    rc32[2 * (off_c[k] + j) + 1] = scale * ay;
   }
 }
 
@@ -380,7 +385,26 @@ std::vector<float> trig_interp(int64_t nc, int64_t nf) {
 
 }  // namespace
 
+struct SetupTimer {
+  bool on;
+  cudaStream_t s;
+  double t0;
+  static double now() {
+    timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return ts.tv_sec + 1e-9 * ts.tv_nsec;
+  }
+  void lap(const char* what) {
+    if (!on) return;
+    cudaStreamSynchronize(s);
+    const double t1 = now();
+    std::fprintf(stderr, "[stokes] two-grid setup: %s %.3f s\n", what, t1 - t0);
+    t0 = t1;
+  }
+};
+
 void twogrid_setup(Geom& g, int q) {
+  SetupTimer tm{std::getenv("STOKES_TRACE") != nullptr, g.stream, SetupTimer::now()};
   TwoGrid& t = g.tg;
   t.ready = false;
   require(q >= 2, "coarsening factor must be >= 2");
@@ -438,6 +462,7 @@ void twogrid_setup(Geom& g, int q) {
   k_coarse_assemble<<<ga, 256, 0, s>>>(Nc, t.pos_c.get(), t.nrm_c.get(), t.w_c.get(), t.selfc_c.get(), t.comp_c.get(),
                                        g.centre.get(), g.outer, t.lu.get());
   STOKES_LAUNCHED();
+  tm.lap("assembly");
   t.piv.alloc(m);
   t.status.alloc(1);
   STOKES_CUDA(cudaMemsetAsync(t.status.get(), 0, sizeof(int), s));
@@ -468,6 +493,7 @@ void twogrid_setup(Geom& g, int q) {
     }
     STOKES_LAUNCHED();
   }
+  tm.lap("LU");
   std::vector<int> hpiv(m);
   int hstatus = 0;
   STOKES_CUDA(cudaMemcpyAsync(hpiv.data(), t.piv.get(), 4 * m, cudaMemcpyDeviceToHost, s));
@@ -480,6 +506,7 @@ void twogrid_setup(Geom& g, int q) {
   t.perm.alloc(m);
   STOKES_CUDA(cudaMemcpyAsync(t.perm.get(), perm.data(), 4 * m, cudaMemcpyHostToDevice, s));
   t.rc.alloc(m);
+  t.rc32.alloc(m);
   t.zc.alloc(m);
   t.h.alloc(2 * g.N);
   // explicit float inverse of the coarse operator: each apply is then one
@@ -487,10 +514,12 @@ void twogrid_setup(Geom& g, int q) {
   t.inv.alloc((size_t)m * m);
   invert_from_lu32(g, t.lu.get(), m, t.perm.get(), t.inv.get());
   t.lu.release();
+  tm.lap("inverse");
   g.prof.end(ps, s);
   // fine blocks of the pores (the wall block is replaced by -2 I)
   bd_setup_pores(g, /*skip_wall=*/true);
   STOKES_CUDA(cudaStreamSynchronize(s));
+  tm.lap("pore blocks");
   t.ready = true;
 }
 
@@ -501,10 +530,10 @@ static void twogrid_apply(Geom& g, const double* r, double* z, const int* done, 
   const int64_t nmax = std::max<int64_t>(1, (g.N + 255) / 256);
   dim3 gr((unsigned)std::min<int64_t>(16, nmax), (unsigned)nc);
   k_restrict<<<gr, 128, 0, s>>>(nc, g.d_off.get(), t.d_off_c.get(), t.d_ioff.get(), t.interp.get(), r, t.rc.get(),
-                                done);
+                                t.rc32.get(), done);
   STOKES_LAUNCHED();
   const int64_t m = 2 * t.Nc;
-  k_dense_gemv32<<<(unsigned)((m + 63) / 64), 256, 0, s>>>(t.inv.get(), m, t.rc.get(), t.zc.get(), done);
+  k_dense_gemv32<<<(unsigned)((m + 63) / 64), 256, 0, s>>>(t.inv.get(), m, t.rc32.get(), t.zc.get(), done);
   STOKES_LAUNCHED();
   dim3 gp((unsigned)std::min<int64_t>(64, nmax), (unsigned)nc);
   k_prolong<<<gp, 128, 0, s>>>(nc, g.outer, g.d_off.get(), t.d_off_c.get(), t.d_ioff.get(), t.interp.get(), r,
