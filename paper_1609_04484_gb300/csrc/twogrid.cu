@@ -54,69 +54,91 @@ __global__ void k_coarse_gather(int64_t Nc, int q, const int64_t* __restrict__ o
   comp_c[ic] = k;
 }
 
+// Float copies of the coarse nodes for the assembly (conversions from
+// double run at the FP64 rate, so they are done once per node here):
+// p = (x_hi, y_hi, x_lo, y_lo), q = (n_x, n_y, w, comp), d = diagonal block.
+__global__ void k_coarse_floats(int64_t Nc, const double2* __restrict__ pos, const double2* __restrict__ nrm,
+                                const double* __restrict__ w, const double4_32a* __restrict__ selfc,
+                                const int* __restrict__ comp, float4* __restrict__ p, float4* __restrict__ qv,
+                                float4* __restrict__ d) {
+  count_launch();
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= Nc) return;
+  const double2 x = pos[i];
+  const float xh = (float)x.x, yh = (float)x.y;
+  p[i] = make_float4(xh, yh, (float)(x.x - (double)xh), (float)(x.y - (double)yh));
+  const double2 n = nrm[i];
+  qv[i] = make_float4((float)n.x, (float)n.y, (float)w[i], __int_as_float(comp[i]));
+  const double4_32a sc = selfc[i];
+  d[i] = make_float4((float)(sc.z * sc.x * sc.x - 0.5), (float)(sc.z * sc.x * sc.y), (float)(sc.z * sc.y * sc.y - 0.5),
+                     0.f);
+}
+
+// Completion centres of all components split into float hi + lo.
+__global__ void k_centre_floats(int n_comp, const double2* __restrict__ centre, float4* __restrict__ c) {
+  count_launch();
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_comp) return;
+  const double2 v = centre[k];
+  const float hx = (float)v.x, hy = (float)v.y;
+  c[k] = make_float4(hx, hy, (float)(v.x - (double)hx), (float)(v.y - (double)hy));
+}
+
 // Dense coarse operator (column-major, leading dimension 2 Nc), one thread
 // per (row node i, column node j) writing the 2 x 2 block A_ij. The result
 // is stored and factorised in float, so it is evaluated in float too, with
 // differences of positions formed from float hi + lo parts (accurate to
 // float precision relative to the distance).
 __global__ void __launch_bounds__(256)
-k_coarse_assemble(int64_t Nc, const double2* __restrict__ pos, const double2* __restrict__ nrm,
-                  const double* __restrict__ w, const double4_32a* __restrict__ selfc, const int* __restrict__ comp,
-                  const double2* __restrict__ centre, int outer, float* __restrict__ A) {
+k_coarse_assemble(int64_t Nc, const float4* __restrict__ P, const float4* __restrict__ Q,
+                  const float4* __restrict__ D, const float4* __restrict__ C, int outer, float* __restrict__ A) {
   count_launch();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= Nc) return;
   const int64_t ld = 2 * Nc;
-  const double2 xid = pos[i];
-  const float xh = (float)xid.x, yh = (float)xid.y;
-  const float xl = (float)(xid.x - (double)xh), yl = (float)(xid.y - (double)yh);
-  const int ci = comp[i];
-  const double2 nid = nrm[i];
+  const float4 pi = P[i];
+  const float4 qi = Q[i];
+  const int ci = __float_as_int(qi.w);
+  const float k4 = (float)kInv4Pi, kp = (float)kInvPi;
   for (int64_t j = blockIdx.y; j < Nc; j += gridDim.y) {
-    const int cj = comp[j];
-    const float wj = (float)w[j];
-    const double2 xjd = pos[j];
-    const float jxh = (float)xjd.x, jyh = (float)xjd.y;
-    const float jxl = (float)(xjd.x - (double)jxh), jyl = (float)(xjd.y - (double)jyh);
+    const float4 pj = P[j];
+    const float4 qj = Q[j];
+    const int cj = __float_as_int(qj.w);
+    const float wj = qj.z;
     float b00, b01, b10, b11;
     if (i == j) {
-      const double4_32a sc = selfc[i];
-      b00 = (float)(sc.z * sc.x * sc.x - 0.5);
-      b01 = (float)(sc.z * sc.x * sc.y);
-      b10 = b01;
-      b11 = (float)(sc.z * sc.y * sc.y - 0.5);
+      const float4 d = D[i];
+      b00 = d.x;
+      b01 = d.y;
+      b10 = d.y;
+      b11 = d.z;
     } else {
-      const double2 nj = nrm[j];
-      const float rx = (xh - jxh) + (xl - jxl), ry = (yh - jyh) + (yl - jyl);
+      const float rx = (pi.x - pj.x) + (pi.z - pj.z), ry = (pi.y - pj.y) + (pi.w - pj.w);
       const float r2 = fmaf(rx, rx, ry * ry);
       const float inv = __frcp_rn(r2);
-      const float c = wj * (float)kInvPi * fmaf(rx, (float)nj.x, ry * (float)nj.y) * inv * inv;
+      const float c = wj * kp * fmaf(rx, qj.x, ry * qj.y) * inv * inv;
       b00 = c * rx * rx;
       b01 = c * rx * ry;
       b10 = b01;
       b11 = c * ry * ry;
     }
     if (cj != outer) {
-      const double2 cc = centre[cj];
-      const float chx = (float)cc.x, chy = (float)cc.y;
-      const float clx = (float)(cc.x - (double)chx), cly = (float)(cc.y - (double)chy);
-      const float rx = (xh - chx) + (xl - clx), ry = (yh - chy) + (yl - cly);
+      const float4 cc = C[cj];
+      const float rx = (pi.x - cc.x) + (pi.z - cc.z), ry = (pi.y - cc.y) + (pi.w - cc.w);
       const float r2 = fmaf(rx, rx, ry * ry);
       const float inv = __frcp_rn(r2);
       const float lg = -0.5f * __logf(r2);
-      const float px = ((jyh - chy) + (jyl - cly)) * wj, py = -((jxh - chx) + (jxl - clx)) * wj;
+      const float px = ((pj.y - cc.y) + (pj.w - cc.w)) * wj, py = -((pj.x - cc.x) + (pj.z - cc.z)) * wj;
       const float ra = ry * inv, rb = -rx * inv;
-      const float k4 = (float)kInv4Pi;
       b00 += k4 * (wj * (lg + rx * rx * inv) + ra * px);
       b01 += k4 * (wj * (rx * ry * inv) + ra * py);
       b10 += k4 * (wj * (rx * ry * inv) + rb * px);
       b11 += k4 * (wj * (lg + ry * ry * inv) + rb * py);
     } else if (ci == outer) {
-      const double2 nj = nrm[j];
-      b00 += (float)(nid.x * nj.x) * wj;
-      b01 += (float)(nid.x * nj.y) * wj;
-      b10 += (float)(nid.y * nj.x) * wj;
-      b11 += (float)(nid.y * nj.y) * wj;
+      b00 += qi.x * wj * qj.x;
+      b01 += qi.x * wj * qj.y;
+      b10 += qi.y * wj * qj.x;
+      b11 += qi.y * wj * qj.y;
     }
     float* col0 = A + (2 * j) * ld + 2 * i;
     float* col1 = col0 + ld;
@@ -458,10 +480,21 @@ void twogrid_setup(Geom& g, int q) {
   const int ps = g.prof.begin(kProfBdSetup, 2.0 * (double)m * m * m, s);
   // assemble and factorise the coarse operator
   t.lu.alloc((size_t)m * m);
-  dim3 ga((unsigned)((Nc + 255) / 256), (unsigned)std::min<int64_t>(Nc, 16384));
-  k_coarse_assemble<<<ga, 256, 0, s>>>(Nc, t.pos_c.get(), t.nrm_c.get(), t.w_c.get(), t.selfc_c.get(), t.comp_c.get(),
-                                       g.centre.get(), g.outer, t.lu.get());
-  STOKES_LAUNCHED();
+  {
+    DevBuf<float4> fp, fq, fd, fc;
+    fp.alloc(Nc);
+    fq.alloc(Nc);
+    fd.alloc(Nc);
+    fc.alloc(nc);
+    k_coarse_floats<<<(unsigned)((Nc + 255) / 256), 256, 0, s>>>(Nc, t.pos_c.get(), t.nrm_c.get(), t.w_c.get(),
+                                                                t.selfc_c.get(), t.comp_c.get(), fp.get(), fq.get(),
+                                                                fd.get());
+    k_centre_floats<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(nc, g.centre.get(), fc.get());
+    dim3 ga((unsigned)((Nc + 255) / 256), (unsigned)std::min<int64_t>(Nc, 16384));
+    k_coarse_assemble<<<ga, 256, 0, s>>>(Nc, fp.get(), fq.get(), fd.get(), fc.get(), g.outer, t.lu.get());
+    STOKES_LAUNCHED();
+    STOKES_CUDA(cudaStreamSynchronize(s));  // scratch goes out of scope
+  }
   tm.lap("assembly");
   t.piv.alloc(m);
   t.status.alloc(1);
