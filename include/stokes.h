@@ -222,6 +222,33 @@ int stokes_profile_enable(stokes_geom* g, int on);
 int stokes_profile_read(stokes_geom* g, int kind, int64_t* launches, double* total_ms,
                         double* total_units);
 
+/* y = A sigma in FP64 without a handle and without allocating GPU memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate (inside a CUDA graph capture, under an allocator that owns
+ * the whole device, on paths where an allocation's device synchronisation
+ * is not allowed). It computes the same operator as stokes_matvec with
+ * STOKES_FP64, reading the boundary arrays directly instead of a handle.
+ *   nodes, normals [2N], weights, curvature [N], sigma, y [2N]: DEVICE arrays
+ *   offsets [n_comp+1], centres [2 n_comp] (the completion centres; the
+ *   wall's entry is ignored): HOST arrays; n_comp, outer_comp as in
+ *   stokes_geometry_create; stream: cudaStream_t (NULL = legacy stream).
+ * Its scratch (offsets, centres, moments, split partial sums) lives in one
+ * 32 MiB file-scope device array that every GPU loading the library keeps
+ * until exit; problems that need more (about 2 million nodes and up) are
+ * rejected with STOKES_EINVAL before anything runs, as are host arrays for
+ * the device arguments and the offsets errors of stokes_geometry_create.
+ * All calls on a device share that array and leave their contents in it;
+ * every call writes all it reads, so nothing needs clearing, but two calls
+ * that overlap on the GPU race and give wrong results. The first call on a
+ * device looks up the array's address (cudaGetSymbolAddress) with that
+ * device current; make it before any stream capture. Asynchronous on
+ * `stream`; returns STOKES_OK, STOKES_EINVAL or STOKES_ECUDA and sets no
+ * stokes_last_error() message. */
+int stokes_matvec_noalloc(const double* nodes, const double* normals, const double* weights,
+                          const double* curvature, const int64_t* offsets, int n_comp,
+                          int outer_comp, const double* centres, const double* sigma, double* y,
+                          void* stream);
+
 /* Number of library kernels that have started on the current device since
  * the library was loaded (each kernel counts itself once when it begins;
  * kernels that return early because a solve already converged count too).

@@ -24,7 +24,7 @@ __all__ = [
     "stokes_gmres_solve", "stokes_eval_velocity", "stokes_last_error", "Geometry",
     "stokes_profile_enable", "stokes_profile_read", "STOKES_PROF_PAIRS_FP64", "STOKES_PROF_PAIRS_FP32",
     "STOKES_PROF_PAIRS_DF64", "STOKES_PROF_EPILOGUE", "STOKES_PROF_BD_APPLY", "STOKES_PROF_ARNOLDI",
-    "STOKES_PROF_BD_SETUP", "stokes_kernel_launches",
+    "STOKES_PROF_BD_SETUP", "stokes_kernel_launches", "stokes_matvec_noalloc",
 ]
 
 STOKES_OK, STOKES_EINVAL, STOKES_ENOMEM, STOKES_ECUDA = 0, -1, -2, -3
@@ -65,6 +65,7 @@ def _load():
         "stokes_last_error": (ctypes.c_char_p, []),
         "stokes_profile_enable": (I, [P, I]),
         "stokes_kernel_launches": (I64, []),
+        "stokes_matvec_noalloc": (I, [P, P, P, P, P, I, I, P, P, P, P]),
         "stokes_profile_read": (I, [P, I, ctypes.POINTER(I64), ctypes.POINTER(D), ctypes.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
@@ -192,6 +193,23 @@ def stokes_profile_read(handle, kind):
     _check(lib.stokes_profile_read(ctypes.c_void_p(handle), int(kind), ctypes.byref(n), ctypes.byref(ms),
                                    ctypes.byref(u)))
     return n.value, ms.value, u.value
+
+
+def stokes_matvec_noalloc(nodes, normals, weights, curvature, offsets, n_comp, outer_comp, centres, sigma, y,
+                          stream=None):
+    """y = A sigma in FP64 without a handle and without allocating GPU memory
+    (for callers that cannot allocate). nodes, normals, weights, curvature,
+    sigma and y must be device arrays (torch CUDA tensors); offsets and
+    centres are host arrays. Returns the status code (STOKES_EINVAL for host
+    arrays or a problem beyond the fixed scratch size)."""
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    cen = np.ascontiguousarray(centres, dtype=np.float64)
+    N = int(off[-1])
+    st = None if stream is None else ctypes.c_void_p(int(stream))
+    return int(lib.stokes_matvec_noalloc(_ptr(nodes, count=2 * N), _ptr(normals, count=2 * N),
+                                         _ptr(weights, count=N), _ptr(curvature, count=N),
+                                         _ptr(off, np.int64), int(n_comp), int(outer_comp), _ptr(cen),
+                                         _ptr(sigma, count=2 * N), _ptr(y, count=2 * N), st))
 
 
 class Geometry:
