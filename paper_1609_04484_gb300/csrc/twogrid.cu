@@ -390,17 +390,25 @@ __global__ void k_prolong(int n_comp, int outer, const int64_t* __restrict__ off
   }
 }
 
-// Real trigonometric interpolation matrix nf x nc (row-major), see the top.
+// Real trigonometric interpolation matrix nf x nc (row-major), see the top,
+// from the closed form of the band-limited (periodic sinc) interpolant:
+//   S(d) = sin(nc d / 2) cot(d / 2) / nc   (nc even),
+//   S(d) = sin(nc d / 2) / (nc sin(d / 2)) (nc odd),  S(0) = 1.
 std::vector<float> trig_interp(int64_t nc, int64_t nf) {
   std::vector<float> P((size_t)(nf * nc));
-  const int64_t K = (nc + 1) / 2 - 1;
   for (int64_t i = 0; i < nf; ++i)
     for (int64_t j = 0; j < nc; ++j) {
       const double d = 2.0 * kPi * (double)i / (double)nf - 2.0 * kPi * (double)j / (double)nc;
-      double v = 1.0;
-      for (int64_t k = 1; k <= K; ++k) v += 2.0 * std::cos((double)k * d);
-      if (nc % 2 == 0) v += std::cos((double)(nc / 2) * d);
-      P[(size_t)(i * nc + j)] = (float)(v / (double)nc);
+      const double sh = std::sin(0.5 * d);
+      double v;
+      if (std::fabs(sh) < 1e-12) {
+        v = 1.0;  // d is a multiple of 2 pi: the sample itself
+      } else if (nc % 2 == 0) {
+        v = std::sin(0.5 * (double)nc * d) * std::cos(0.5 * d) / (sh * (double)nc);
+      } else {
+        v = std::sin(0.5 * (double)nc * d) / (sh * (double)nc);
+      }
+      P[(size_t)(i * nc + j)] = (float)v;
     }
   return P;
 }
