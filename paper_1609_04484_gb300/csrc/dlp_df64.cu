@@ -53,7 +53,6 @@ k_dlp_pairs_df64(int64_t N, const float2* __restrict__ grid, const float4* __res
   const df32 X = dlp::df_from_double(x.x - gx), Y = dlp::df_from_double(x.y - gy);
   const int64_t j0 = blockIdx.y * chunk;
   const int64_t j1 = imin64(N, j0 + chunk);
-  const int64_t iself = self_skip ? i : -1;
   double ux = 0.0, uy = 0.0;
   for (int64_t t0 = j0; t0 < j1; t0 += kTile) {
     __syncthreads();
@@ -74,7 +73,6 @@ k_dlp_pairs_df64(int64_t N, const float2* __restrict__ grid, const float4* __res
       }
     }
     __syncthreads();
-    const int64_t jb = t0 - iself;
     df32 ax = {0.f, 0.f}, ay = {0.f, 0.f};
 #pragma unroll 2
     for (int q = 0; q < kTile; ++q) {
@@ -93,7 +91,9 @@ k_dlp_pairs_df64(int64_t N, const float2* __restrict__ grid, const float4* __res
       df32 ry = dlp::fast_two_sum(GY - gq.y, ly.h);
       ry.l += ly.l;
       // rho^2 = rx^2 + ry^2
-      const float px = rx.h * rx.h;
+      // + 1e-30: the self pair (r = 0, so r.a = r.sigma = 0) gets a finite
+      // reciprocal and contributes exactly 0; for other pairs rho^2 >> 1e-30
+      const float px = fmaf(rx.h, rx.h, 1e-30f);
       float ex = fmaf(rx.h, rx.h, -px);
       ex = fmaf(rx.h + rx.h, rx.l, ex);
       const float py = ry.h * ry.h;
@@ -101,7 +101,6 @@ k_dlp_pairs_df64(int64_t N, const float2* __restrict__ grid, const float4* __res
       ey = fmaf(ry.h + ry.h, ry.l, ey);
       df32 r2 = dlp::two_sum(px, py);
       r2 = dlp::fast_two_sum(r2.h, r2.l + (ex + ey));
-      if (q + jb == 0) r2 = {1.f, 0.f};  // r = 0: the pair contributes 0
       // 1 / rho^2: one Newton step from the correctly rounded reciprocal
       const float y0 = __frcp_rn(r2.h);
       float t = fmaf(-r2.h, y0, 1.0f);

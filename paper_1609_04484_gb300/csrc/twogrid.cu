@@ -149,23 +149,52 @@ k_coarse_assemble(int64_t Nc, const float4* __restrict__ P, const float4* __rest
   }
 }
 
-// y = X x for a dense column-major float matrix (double vectors): CTA per
-// 64 rows, the 256 threads split the columns in four interleaved phases.
+// y = X x for a dense column-major float matrix: CTA per 256 rows; thread t
+// of 256 owns rows 4 (t mod 64) .. + 3 (one float4 per column) and the
+// columns q = t / 64 (mod 4); partial sums are combined in shared memory.
 __global__ void __launch_bounds__(256)
 k_dense_gemv32(const float* __restrict__ X, int64_t m, const float* __restrict__ x, double* __restrict__ y,
                const int* __restrict__ done) {
   count_launch();
   if (done && *done) return;
-  __shared__ float red[4][64];
-  const int64_t r0 = blockIdx.x * (int64_t)64;
-  const int rr = threadIdx.x & 63, ph = threadIdx.x >> 6;
-  const int64_t r = r0 + rr;
-  float acc = 0.f;
-  if (r < m)
-    for (int64_t q = ph; q < m; q += 4) acc = fmaf(X[q * m + r], x[q], acc);
-  red[ph][rr] = acc;
+  __shared__ float4 red[4][64];
+  const int64_t r0 = blockIdx.x * (int64_t)256;
+  const int tr = threadIdx.x & 63, ph = threadIdx.x >> 6;
+  const int64_t r = r0 + 4 * tr;
+  float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+  if ((m & 3) == 0 && r + 3 < m) {  // float4 loads need 16-byte aligned rows
+    int64_t q = ph;
+    for (; q + 4 < m; q += 8) {
+      const float4 u = *reinterpret_cast<const float4*>(X + q * m + r);
+      const float4 v = *reinterpret_cast<const float4*>(X + (q + 4) * m + r);
+      const float xu = x[q], xv = x[q + 4];
+      a0.x = fmaf(u.x, xu, a0.x); a0.y = fmaf(u.y, xu, a0.y); a0.z = fmaf(u.z, xu, a0.z); a0.w = fmaf(u.w, xu, a0.w);
+      a1.x = fmaf(v.x, xv, a1.x); a1.y = fmaf(v.y, xv, a1.y); a1.z = fmaf(v.z, xv, a1.z); a1.w = fmaf(v.w, xv, a1.w);
+    }
+    for (; q < m; q += 4) {
+      const float4 u = *reinterpret_cast<const float4*>(X + q * m + r);
+      const float xu = x[q];
+      a0.x = fmaf(u.x, xu, a0.x); a0.y = fmaf(u.y, xu, a0.y); a0.z = fmaf(u.z, xu, a0.z); a0.w = fmaf(u.w, xu, a0.w);
+    }
+  } else if (r < m) {
+    for (int64_t q = ph; q < m; q += 4) {
+      const float xu = x[q];
+      const float* col = X + q * m + r;
+      a0.x = fmaf(col[0], xu, a0.x);
+      if (r + 1 < m) a0.y = fmaf(col[1], xu, a0.y);
+      if (r + 2 < m) a0.z = fmaf(col[2], xu, a0.z);
+      if (r + 3 < m) a0.w = fmaf(col[3], xu, a0.w);
+    }
+  }
+  red[ph][tr] = make_float4(a0.x + a1.x, a0.y + a1.y, a0.z + a1.z, a0.w + a1.w);
   __syncthreads();
-  if (ph == 0 && r < m) y[r] = (double)((red[0][rr] + red[1][rr]) + (red[2][rr] + red[3][rr]));
+  if (ph == 0) {
+    const float4 s0 = red[0][tr], s1 = red[1][tr], s2 = red[2][tr], s3 = red[3][tr];
+    const float o[4] = {(s0.x + s1.x) + (s2.x + s3.x), (s0.y + s1.y) + (s2.y + s3.y),
+                        (s0.z + s1.z) + (s2.z + s3.z), (s0.w + s1.w) + (s2.w + s3.w)};
+    for (int c = 0; c < 4; ++c)
+      if (r + c < m) y[r + c] = (double)o[c];
+  }
 }
 
 // ---- float blocked LU (right-looking, partial pivoting) ----
@@ -574,7 +603,7 @@ static void twogrid_apply(Geom& g, const double* r, double* z, const int* done, 
                                 t.rc32.get(), done);
   STOKES_LAUNCHED();
   const int64_t m = 2 * t.Nc;
-  k_dense_gemv32<<<(unsigned)((m + 63) / 64), 256, 0, s>>>(t.inv.get(), m, t.rc32.get(), t.zc.get(), done);
+  k_dense_gemv32<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(t.inv.get(), m, t.rc32.get(), t.zc.get(), done);
   STOKES_LAUNCHED();
   dim3 gp((unsigned)std::min<int64_t>(64, nmax), (unsigned)nc);
   k_prolong<<<gp, 128, 0, s>>>(nc, g.outer, g.d_off.get(), t.d_off_c.get(), t.d_ioff.get(), t.interp.get(), r,
