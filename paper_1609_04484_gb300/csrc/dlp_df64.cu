@@ -91,9 +91,7 @@ k_dlp_pairs_df64(int64_t N, const float2* __restrict__ grid, const float4* __res
       df32 ry = dlp::fast_two_sum(GY - gq.y, ly.h);
       ry.l += ly.l;
       // rho^2 = rx^2 + ry^2
-      // + 1e-30: the self pair (r = 0, so r.a = r.sigma = 0) gets a finite
-      // reciprocal and contributes exactly 0; for other pairs rho^2 >> 1e-30
-      const float px = fmaf(rx.h, rx.h, 1e-30f);
+      const float px = rx.h * rx.h;
       float ex = fmaf(rx.h, rx.h, -px);
       ex = fmaf(rx.h + rx.h, rx.l, ex);
       const float py = ry.h * ry.h;
@@ -101,6 +99,10 @@ k_dlp_pairs_df64(int64_t N, const float2* __restrict__ grid, const float4* __res
       ey = fmaf(ry.h + ry.h, ry.l, ey);
       df32 r2 = dlp::two_sum(px, py);
       r2 = dlp::fast_two_sum(r2.h, r2.l + (ex + ey));
+      // + 1e-30 after normalisation: the self pair (r = 0, so r.a = r.sigma
+      // = 0) gets a finite reciprocal and contributes exactly 0; for any other
+      // pair rho^2 >> 1e-30 and the addition rounds away
+      r2.h += 1e-30f;
       // 1 / rho^2: one Newton step from the correctly rounded reciprocal
       const float y0 = __frcp_rn(r2.h);
       float t = fmaf(-r2.h, y0, 1.0f);
