@@ -64,6 +64,9 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--kernel-bench", action="store_true",
                    help="time only operator applications (A sigma) of each precision on the workload")
+    p.add_argument("--batch-bench", action="store_true",
+                   help="time the batched operator and lockstep solve on a multi-geometry batch")
+    p.add_argument("--batch-geoms", type=int, default=16)
     p.add_argument("--reps", type=int, default=5)
     p.add_argument("--precisions", default="fp32,df64,fp64")
     return p.parse_args()
@@ -249,8 +252,96 @@ def kernel_bench(args):
     G.close()
 
 
+def batch_workload(n):
+    """Uneven batch of porous pipes: pore counts uniform in [20, 120], 64 or
+    128 nodes per pore, 1024 or 2048 wall nodes (the batch configuration's
+    shape, scaled down so that every geometry's block-diagonal setup and
+    dense oracle checks stay small)."""
+    import stokes_inputs as si
+    return [si.cached_geometry(f"batchsmall{i}", 0) for i in range(n)]
+
+
+def batch_bench(args):
+    """Batched operator (all geometries x 4 right-hand sides in one
+    persistent launch) against the single-geometry kernels, and the lockstep
+    mixed-precision solve against one solve per system."""
+    import torch
+    import paper_1609_04484_gb300 as S
+    import stokes_inputs as si
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    geoms = batch_workload(args.batch_geoms)
+    R = 4
+    Gs = [S.Geometry(g, stream=stream.cuda_stream) for g in geoms]
+    hs = [G.handle for G in Gs]
+    for G in Gs:
+        S.stokes_precond_setup(G.handle, S.STOKES_PC_BLOCKDIAG)
+    sig = [torch.tensor(si.random_density(g, r).reshape(-1), device=dev) for g in geoms for r in range(R)]
+    ys = [torch.empty_like(x) for x in sig]
+    pairs = float(sum(g.n_nodes ** 2 for g in geoms)) * R
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cfg = {"workload": f"{len(geoms)} porous pipes x {R} right-hand sides (pores 20-120, 64/128 nodes per pore, "
+                       f"1024/2048 wall nodes)", "nodes": [g.n_nodes for g in geoms]}
+    for name, prec in (("fp32", S.STOKES_FP32), ("df64", S.STOKES_DF64)):
+        for _ in range(max(1, args.warmup)):
+            S.stokes_batch_matvec(hs, R, sig, ys, prec)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.reps):
+            S.stokes_batch_matvec(hs, R, sig, ys, prec)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t_batch = ev0.elapsed_time(ev1) / args.reps
+        ev0.record(stream)
+        for _ in range(args.reps):
+            for k, G in enumerate(Gs):
+                for r in range(R):
+                    S.stokes_matvec(G.handle, sig[k * R + r], ys[k * R + r], prec)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t_single = ev0.elapsed_time(ev1) / args.reps
+        print(json.dumps({"batch_operator": name, "config": cfg["workload"], "pair_rhs_per_launch": pairs,
+                          "batch_ms": round(t_batch, 3), "one_call_per_system_ms": round(t_single, 3),
+                          "gpairs_rhs_per_s": round(pairs / (t_batch * 1e-3) / 1e9, 1),
+                          "speedup": round(t_single / t_batch, 2)}), flush=True)
+    fs = []
+    for g in geoms:
+        fs += [torch.tensor(b.reshape(-1), device=dev) for b in
+               (si.pipe_bc(g), si.reversed_pipe_bc(g), si.outer_shear_bc(g), si.stokeslet_rotlet_bc(g, 0))]
+    for attempt in range(2):  # the first call also captures the cycle graph
+        xs = [torch.zeros_like(f) for f in fs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        iters, relres, status = S.stokes_batch_solve(hs, R, fs, xs, tol=args.tol, restart=50, max_iter=3000,
+                                                     precision=S.STOKES_MIXED_IR)
+        torch.cuda.synchronize()
+        t_batch = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    it_single = []
+    for k, G in enumerate(Gs):
+        for r in range(R):
+            x1 = torch.zeros_like(fs[k * R + r])
+            code, it, rr, _ = S.stokes_gmres_solve(G.handle, fs[k * R + r], x1, tol=args.tol, restart=50,
+                                                   max_iter=3000, precision=S.STOKES_MIXED_IR)
+            it_single.append(it)
+    torch.cuda.synchronize()
+    t_single = time.perf_counter() - t0
+    print(json.dumps({"batch_solve": "mixed (FP32 inner, FP64 outer), block diagonal, FGMRES(50)",
+                      "config": cfg["workload"], "systems": len(fs), "tol": args.tol,
+                      "batch_s": round(t_batch, 3), "one_solve_per_system_s": round(t_single, 3),
+                      "speedup": round(t_single / t_batch, 2), "iters_max": max(iters),
+                      "iters_mean": round(float(np.mean(iters)), 1), "single_iters_mean":
+                      round(float(np.mean(it_single)), 1), "relres_max": max(relres),
+                      "all_converged": all(s == S.STOKES_OK for s in status)}), flush=True)
+    for G in Gs:
+        G.close()
+
+
 def main():
     args = parse_args()
+    if args.batch_bench:
+        batch_bench(args)
+        return
     if args.kernel_bench:
         kernel_bench(args)
         return

@@ -249,6 +249,105 @@ int stokes_matvec_noalloc(const double* nodes, const double* normals, const doub
                           int outer_comp, const double* centres, const double* sigma, double* y,
                           void* stream);
 
+/* Launch-shape autotuner of the pair kernels (the paper has no
+ * counterpart: its matvec is an FMM on a CPU; here the direct pair sum's
+ * best CTA shape depends on the problem size and the arithmetic).
+ *
+ * Each pair kernel (precision STOKES_FP64, STOKES_FP32 or STOKES_DF64) is
+ * compiled in a few shape variants: threads per CTA, targets accumulated
+ * per thread, sources per shared-memory tile. Variant 0 is the built-in
+ * default. The source range is split so that the grid holds about
+ * `ctas_per_sm` CTAs per SM (152 SMs). A handle uses, in this order: the
+ * shape set on it (stokes_set_pair_shape or stokes_autotune), the
+ * process-wide cache entry of its size class (precision, ceil(log2 N),
+ * ceil(log2 T); N sources, T targets), the default (variant 0, 4 CTAs/SM).
+ * Every shape computes the same sums in the same order within a thread; the
+ * results differ between shapes only through the source splitting
+ * (rounding of the partial sums). */
+
+/* Number of compiled shape variants of a precision's pair kernel, or
+ * STOKES_EINVAL for an unknown precision. */
+int stokes_pair_shape_count(int precision);
+
+/* Threads per CTA, targets per thread and sources per tile of a variant
+ * (outputs may be NULL). STOKES_EINVAL for unknown precision or variant. */
+int stokes_pair_shape_info(int precision, int variant, int* threads, int* targets_per_thread, int* tile);
+
+/* Fix the shape of a precision's pair kernel on a handle; variant < 0 clears
+ * it (back to the cache or the default). ctas_per_sm in [1, 64]. */
+int stokes_set_pair_shape(stokes_geom* g, int precision, int variant, int ctas_per_sm);
+
+/* The shape a handle would use for n_targets targets (>= 1). */
+int stokes_get_pair_shape(stokes_geom* g, int precision, int64_t n_targets, int* variant, int* ctas_per_sm);
+
+/* Time every (variant, ctas_per_sm in {2, 4, 8}) of the pair kernel alone on
+ * the handle's nodes as targets: one warm-up launch and `reps` (1..100) timed
+ * launches each, CUDA events on the handle's stream. The fastest is set on
+ * the handle and stored in the cache under the handle's size class (T = N).
+ * Outputs (may be NULL): the chosen variant and ctas_per_sm and its time per
+ * launch in ms. Synchronises the stream. Errors: STOKES_EINVAL, STOKES_ECUDA. */
+int stokes_autotune(stokes_geom* g, int precision, int reps, int* variant, int* ctas_per_sm, double* best_ms);
+
+/* The process-wide cache (host only; these calls need no GPU).
+ * insert: set the entry of a size class (validated against this build's
+ *   variants); lookup: *variant = -1 when there is no entry;
+ * save: write all entries to `path` as JSON lines (written to path.tmp, then
+ *   renamed), each with precision, log2_sources, log2_targets, variant,
+ *   threads, targets_per_thread, tile, ctas_per_sm, ms;
+ * load: merge the entries of such a file; lines that do not parse, or whose
+ *   variant index or shape does not match this build, are skipped;
+ *   *n_loaded (may be NULL) counts the entries taken. A missing file is
+ *   STOKES_EINVAL. */
+int stokes_tune_cache_insert(int precision, int64_t n_sources, int64_t n_targets, int variant, int ctas_per_sm,
+                             double ms);
+int stokes_tune_cache_lookup(int precision, int64_t n_sources, int64_t n_targets, int* variant, int* ctas_per_sm,
+                             double* ms);
+int stokes_tune_cache_clear(void);
+int stokes_tune_cache_save(const char* path);
+int stokes_tune_cache_load(const char* path, int* n_loaded);
+
+/* Batched operator over many geometries and right-hand sides (the paper
+ * has no counterpart; it treats one geometry and one right-hand side at a
+ * time). For geometries k < n_geoms and right-hand sides r < n_rhs (1..4),
+ * system s = k n_rhs + r:
+ *   y[s] = A_k sigma[s]   (the operator of stokes_matvec)
+ * sigma[s], y[s]: DEVICE arrays of 2 N_k doubles; the pointer arrays
+ * themselves are host memory. The pair sums of all systems run in ONE
+ * persistent launch whose CTAs take work items (geometry, block of targets,
+ * range of sources) from an atomic counter; the n_rhs densities of a
+ * geometry share each pair's geometry (r, 1/rho^2, r.a). precision:
+ * STOKES_FP32 or STOKES_DF64 (the arithmetic of stokes_matvec's operator of
+ * that precision; results differ from it only in the order of the partial
+ * sums). All handles must share one CUDA stream; the call synchronises it.
+ * At most 1024 systems. Errors: STOKES_EINVAL, STOKES_ENOMEM, STOKES_ECUDA. */
+int stokes_batch_matvec(stokes_geom* const* geoms, int n_geoms, int n_rhs, const double* const* sigma,
+                        double* const* y, int precision);
+
+/* Solve A_k sigma[s] = f[s] for every system s = k n_rhs + r (layout as in
+ * stokes_batch_matvec) by right-preconditioned flexible GMRES(restart)
+ * (Sec. 4) run on all systems in lockstep: each step applies every system's
+ * preconditioner (the geometry's last stokes_precond_setup* in float
+ * copies; none if never set up), the batched operator and a classical
+ * Gram-Schmidt step repeated once, all systems' reductions and Givens
+ * rotations in shared launches. A restart cycle is captured once as a CUDA
+ * graph and replayed; converged systems' kernels return at once. True
+ * residuals |f - A sigma| / |f| are taken with the native FP64 operator at
+ * every restart.
+ *   precision STOKES_DF64 (double-float operator in the cycles) or
+ *             STOKES_MIXED_IR (FP64 residuals per system, corrections by
+ *             lockstep FP32 cycles to max(1e-4, tol / (2 relres)), as in
+ *             stokes_gmres_solve)
+ *   restart 1..1000; max_iter >= 1 (per system, inner iterations for IR)
+ *   sigma[s] in: initial guess (DEVICE); out: solution
+ *   iters, relres, status: HOST arrays of n_geoms n_rhs entries (may be
+ *   NULL): iterations, true relative residual and STOKES_OK,
+ *   STOKES_ENOTCONV or STOKES_EBREAKDOWN of each system.
+ * The call returns STOKES_OK when it ran (per-system outcomes are in
+ * status), else STOKES_EINVAL, STOKES_ENOMEM or STOKES_ECUDA. */
+int stokes_batch_solve(stokes_geom* const* geoms, int n_geoms, int n_rhs, const double* const* f, double tol,
+                       int restart, int max_iter, int precision, double* const* sigma, int* iters,
+                       double* relres, int* status);
+
 /* Number of library kernels that have started on the current device since
  * the library was loaded (each kernel counts itself once when it begins;
  * kernels that return early because a solve already converged count too).

@@ -25,6 +25,9 @@ __all__ = [
     "stokes_profile_enable", "stokes_profile_read", "STOKES_PROF_PAIRS_FP64", "STOKES_PROF_PAIRS_FP32",
     "STOKES_PROF_PAIRS_DF64", "STOKES_PROF_EPILOGUE", "STOKES_PROF_BD_APPLY", "STOKES_PROF_ARNOLDI",
     "STOKES_PROF_BD_SETUP", "stokes_kernel_launches", "stokes_matvec_noalloc",
+    "stokes_pair_shape_count", "stokes_pair_shape_info", "stokes_set_pair_shape", "stokes_get_pair_shape",
+    "stokes_autotune", "stokes_tune_cache_insert", "stokes_tune_cache_lookup", "stokes_tune_cache_clear",
+    "stokes_tune_cache_save", "stokes_tune_cache_load", "stokes_batch_matvec", "stokes_batch_solve",
 ]
 
 STOKES_OK, STOKES_EINVAL, STOKES_ENOMEM, STOKES_ECUDA = 0, -1, -2, -3
@@ -67,6 +70,18 @@ def _load():
         "stokes_kernel_launches": (I64, []),
         "stokes_matvec_noalloc": (I, [P, P, P, P, P, I, I, P, P, P, P]),
         "stokes_profile_read": (I, [P, I, ctypes.POINTER(I64), ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "stokes_pair_shape_count": (I, [I]),
+        "stokes_pair_shape_info": (I, [I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "stokes_set_pair_shape": (I, [P, I, I, I]),
+        "stokes_get_pair_shape": (I, [P, I, I64, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "stokes_autotune": (I, [P, I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]),
+        "stokes_tune_cache_insert": (I, [I, I64, I64, I, I, D]),
+        "stokes_tune_cache_lookup": (I, [I, I64, I64, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]),
+        "stokes_tune_cache_clear": (I, []),
+        "stokes_tune_cache_save": (I, [ctypes.c_char_p]),
+        "stokes_tune_cache_load": (I, [ctypes.c_char_p, ctypes.POINTER(I)]),
+        "stokes_batch_matvec": (I, [P, I, I, P, P, I]),
+        "stokes_batch_solve": (I, [P, I, I, P, D, I, I, I, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -210,6 +225,102 @@ def stokes_matvec_noalloc(nodes, normals, weights, curvature, offsets, n_comp, o
                                          _ptr(weights, count=N), _ptr(curvature, count=N),
                                          _ptr(off, np.int64), int(n_comp), int(outer_comp), _ptr(cen),
                                          _ptr(sigma, count=2 * N), _ptr(y, count=2 * N), st))
+
+
+def stokes_pair_shape_count(precision) -> int:
+    n = int(lib.stokes_pair_shape_count(int(precision)))
+    if n < 0:
+        raise StokesError(n, "unknown precision")
+    return n
+
+
+def stokes_pair_shape_info(precision, variant):
+    """Returns (threads, targets_per_thread, tile) of a compiled variant."""
+    th, tpt, tile = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib.stokes_pair_shape_info(int(precision), int(variant), ctypes.byref(th), ctypes.byref(tpt),
+                                      ctypes.byref(tile)))
+    return th.value, tpt.value, tile.value
+
+
+def stokes_set_pair_shape(handle, precision, variant, ctas_per_sm=4):
+    _check(lib.stokes_set_pair_shape(ctypes.c_void_p(handle), int(precision), int(variant), int(ctas_per_sm)))
+
+
+def stokes_get_pair_shape(handle, precision, n_targets):
+    """Returns (variant, ctas_per_sm) the handle uses for n_targets targets."""
+    v, c = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib.stokes_get_pair_shape(ctypes.c_void_p(handle), int(precision), ctypes.c_int64(n_targets),
+                                     ctypes.byref(v), ctypes.byref(c)))
+    return v.value, c.value
+
+
+def stokes_autotune(handle, precision, reps=2):
+    """Times every shape of the pair kernel; returns (variant, ctas_per_sm, ms)."""
+    v, c, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+    _check(lib.stokes_autotune(ctypes.c_void_p(handle), int(precision), int(reps), ctypes.byref(v),
+                               ctypes.byref(c), ctypes.byref(ms)))
+    return v.value, c.value, ms.value
+
+
+def stokes_tune_cache_insert(precision, n_sources, n_targets, variant, ctas_per_sm, ms=0.0):
+    _check(lib.stokes_tune_cache_insert(int(precision), ctypes.c_int64(n_sources), ctypes.c_int64(n_targets),
+                                        int(variant), int(ctas_per_sm), float(ms)))
+
+
+def stokes_tune_cache_lookup(precision, n_sources, n_targets):
+    """Returns (variant, ctas_per_sm, ms); variant -1 when absent."""
+    v, c, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+    _check(lib.stokes_tune_cache_lookup(int(precision), ctypes.c_int64(n_sources), ctypes.c_int64(n_targets),
+                                        ctypes.byref(v), ctypes.byref(c), ctypes.byref(ms)))
+    return v.value, c.value, ms.value
+
+
+def stokes_tune_cache_clear():
+    _check(lib.stokes_tune_cache_clear())
+
+
+def stokes_tune_cache_save(path):
+    _check(lib.stokes_tune_cache_save(str(path).encode()))
+
+
+def stokes_tune_cache_load(path) -> int:
+    n = ctypes.c_int(0)
+    _check(lib.stokes_tune_cache_load(str(path).encode(), ctypes.byref(n)))
+    return n.value
+
+
+def _ptr_array(handles_or_arrays, counts=None):
+    """A C array of pointers (void*[]) to handles or device arrays."""
+    vals = []
+    for k, a in enumerate(handles_or_arrays):
+        if isinstance(a, int):
+            vals.append(a)
+        else:
+            vals.append(_ptr(a, count=None if counts is None else counts[k]).value)
+    return (ctypes.c_void_p * len(vals))(*vals)
+
+
+def stokes_batch_matvec(handles, n_rhs, sigma, y, precision=STOKES_FP32):
+    """y[k * n_rhs + r] = A_k sigma[k * n_rhs + r] for every geometry k and
+    right-hand side r (device tensors), one persistent pair launch."""
+    ns = [2 * stokes_geometry_num_nodes(h) for h in handles for _ in range(n_rhs)]
+    _check(lib.stokes_batch_matvec(_ptr_array(handles), len(handles), int(n_rhs), _ptr_array(sigma, ns),
+                                   _ptr_array(y, ns), int(precision)))
+
+
+def stokes_batch_solve(handles, n_rhs, f, sigma, tol=1e-8, restart=50, max_iter=2000,
+                       precision=STOKES_MIXED_IR):
+    """Lockstep flexible GMRES of all (geometry, right-hand side) systems;
+    solves in place into the device tensors `sigma` (initial guesses).
+    Returns (iters, relres, status) lists per system."""
+    S = len(handles) * n_rhs
+    ns = [2 * stokes_geometry_num_nodes(h) for h in handles for _ in range(n_rhs)]
+    it = (ctypes.c_int * S)()
+    rr = (ctypes.c_double * S)()
+    st = (ctypes.c_int * S)()
+    _check(lib.stokes_batch_solve(_ptr_array(handles), len(handles), int(n_rhs), _ptr_array(f, ns), float(tol),
+                                  int(restart), int(max_iter), int(precision), _ptr_array(sigma, ns), it, rr, st))
+    return list(it), list(rr), list(st)
 
 
 class Geometry:

@@ -4,12 +4,9 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "internal.cuh"
-
-struct stokes_geom {
-  stokes::Geom* g;
-};
 
 namespace stokes {
 Geom* geometry_create(const double*, const double*, const double*, const double*, const int64_t*, int, int,
@@ -41,6 +38,14 @@ int guarded(F&& fn) {
 
 using stokes::DevBuf;
 using stokes::Geom;
+
+}  // namespace
+
+int stokes::guarded_call(void (*fn)(void*), void* ctx) {
+  return guarded([&] { fn(ctx); });
+}
+
+namespace {
 
 // A device view of a caller array: the caller's pointer if it is device
 // memory, else a handle-owned staging buffer filled from the host.
@@ -253,10 +258,34 @@ int64_t stokes_kernel_launches(void) {
   try {
     return (int64_t)(stokes::launches_geometry() + stokes::launches_dlp_f64() + stokes::launches_dlp_f32() +
                      stokes::launches_dlp_df64() + stokes::launches_bd() + stokes::launches_bd_trsv() + stokes::launches_bd_inv32() + stokes::launches_twogrid() +
-                     stokes::launches_gmres());
+                     stokes::launches_gmres() + stokes::launches_batch());
   } catch (...) {
     return -1;
   }
+}
+
+int stokes_batch_matvec(stokes_geom* const* geoms, int n_geoms, int n_rhs, const double* const* sigma,
+                        double* const* y, int precision) {
+  return guarded([&] {
+    stokes::require(geoms && sigma && y, "null argument");
+    stokes::require(n_geoms >= 1, "n_geoms must be >= 1");
+    std::vector<Geom*> gs(n_geoms);
+    for (int k = 0; k < n_geoms; ++k) gs[k] = &handle(geoms[k]);
+    stokes::batch_matvec(gs.data(), n_geoms, n_rhs, sigma, y, precision);
+  });
+}
+
+int stokes_batch_solve(stokes_geom* const* geoms, int n_geoms, int n_rhs, const double* const* f, double tol,
+                       int restart, int max_iter, int precision, double* const* sigma, int* iters,
+                       double* relres, int* status) {
+  return guarded([&] {
+    stokes::require(geoms && f && sigma, "null argument");
+    stokes::require(n_geoms >= 1, "n_geoms must be >= 1");
+    std::vector<Geom*> gs(n_geoms);
+    for (int k = 0; k < n_geoms; ++k) gs[k] = &handle(geoms[k]);
+    stokes::batch_solve(gs.data(), n_geoms, n_rhs, f, tol, restart, max_iter, precision, sigma, iters, relres,
+                        status);
+  });
 }
 
 const char* stokes_last_error(void) { return g_last_error.c_str(); }

@@ -12,11 +12,12 @@ namespace dlp {
 
 constexpr int kEpiPores = 256;
 
-// Split the sources so that the grid has ~4 CTAs per SM; each split covers
-// a whole number of `tile`-sized source tiles.
-inline void pair_launch_shape(int64_t N, int64_t T, int tb, int tile, int& splits, int64_t& chunk) {
+// Split the sources so that the grid has ~ctas_per_sm CTAs per SM (152 SMs);
+// each split covers a whole number of `tile`-sized source tiles.
+inline void pair_launch_shape(int64_t N, int64_t T, int tb, int tile, int& splits, int64_t& chunk,
+                              int ctas_per_sm = 4) {
   const int64_t tblocks = (T + tb - 1) / tb;
-  int64_t want = (4 * 152 + tblocks - 1) / tblocks;
+  int64_t want = ((int64_t)ctas_per_sm * 152 + tblocks - 1) / tblocks;
   const int64_t max_split = (N + tile - 1) / tile;
   if (want > max_split) want = max_split;
   if (want < 1) want = 1;
@@ -139,7 +140,8 @@ struct PoreDF {
 
 template <int kMode>
 __global__ void __launch_bounds__(256)
-k_epilogue(int64_t T, int S, const double2* __restrict__ part, int boundary, const double2* __restrict__ tgt,
+k_epilogue(int64_t T, int S, const double2* __restrict__ part, int64_t pstride, int boundary,
+           const double2* __restrict__ tgt,
            const double4_32a* __restrict__ selfc, const double2* __restrict__ sig, const int* __restrict__ comp,
            int outer, const double2* __restrict__ nrm, int M, const int* __restrict__ pore_ids,
            const double2* __restrict__ centre, const double4_32a* __restrict__ mom,
@@ -156,7 +158,7 @@ k_epilogue(int64_t T, int S, const double2* __restrict__ part, int boundary, con
   double2 x = make_double2(0.0, 0.0);
   if (live) {
     for (int s = 0; s < S; ++s) {
-      const double2 p = part[s * T + i];
+      const double2 p = part[s * pstride + i];
       ax += p.x;
       ay += p.y;
     }
@@ -292,12 +294,16 @@ inline bool ensure_log_table(Geom& g) {
   return true;
 }
 
+// part: split partial sums, split s of target i at part[s * pstride + i];
+// mom: the component moments of sigma.
 template <int kMode>
 inline void launch_epilogue(Geom& g, int64_t T, int splits, bool boundary, const double2* targets,
-                            const double2* sigma, double2* y, const int* done) {
+                            const double2* sigma, double2* y, const int* done, const double2* part = nullptr,
+                            int64_t pstride = -1, const double4_32a* mom = nullptr) {
   k_epilogue<kMode><<<(unsigned)((T + 255) / 256), 256, 0, g.stream>>>(
-      T, splits, g.part.get(), boundary ? 1 : 0, targets, g.selfc.get(), sigma, g.comp.get(), g.outer,
-      g.nrm.get(), g.M, g.pore_ids.get(), g.centre.get(), g.mom.get(), g.logtab.get(), y, done);
+      T, splits, part ? part : g.part.get(), pstride >= 0 ? pstride : T, boundary ? 1 : 0, targets, g.selfc.get(),
+      sigma, g.comp.get(), g.outer, g.nrm.get(), g.M, g.pore_ids.get(), g.centre.get(), mom ? mom : g.mom.get(),
+      g.logtab.get(), y, done);
   STOKES_LAUNCHED();
 }
 

@@ -99,9 +99,9 @@ __global__ void k_prep_nodes(int64_t N, const double2* __restrict__ pos, const d
 
 }  // namespace
 
-void moments_f64(Geom& g, const double2* sigma, const int* done) {
+void moments_f64(Geom& g, const double2* sigma, const int* done, double4_32a* out) {
   k_moments_f64<<<g.n_comp, 256, 0, g.stream>>>(g.pos.get(), g.nrm.get(), g.w.get(), g.d_off.get(),
-                                                g.centre.get(), sigma, g.mom.get(), done);
+                                                g.centre.get(), sigma, out ? out : g.mom.get(), done);
   STOKES_LAUNCHED();
 }
 

@@ -180,6 +180,17 @@ struct TwoGrid {
   DevBuf<int> d_pore_ids;
 };
 
+// Launch shape of a pair kernel: a compiled variant (threads per CTA,
+// targets per thread, sources per shared-memory tile) and the number of CTAs
+// per SM that the source splitting aims for.
+struct PairVariant {
+  int threads, tpt, tile;
+};
+struct PairShape {
+  int variant = -1;     // < 0: not chosen (defaults or the tuner's cache decide)
+  int ctas_per_sm = 4;
+};
+
 struct Geom {
   int64_t N = 0;
   int n_comp = 0;
@@ -218,6 +229,10 @@ struct Geom {
   DevBuf<double2> stage_in, stage_out, stage_tgt;  // host<->device staging
   DevBuf<double2> tmp2;
 
+  // launch shapes of the pair kernels set on this handle (by the tuner or
+  // explicitly), indexed by precision (FP64, FP32, DF64)
+  PairShape shape[3];
+
   BlockDiag bd;
   TwoGrid tg;
   Krylov kr;
@@ -234,15 +249,34 @@ unsigned long long launches_bd_trsv();
 unsigned long long launches_bd_inv32();
 unsigned long long launches_twogrid();
 unsigned long long launches_gmres();
+unsigned long long launches_batch();
 
 // ---- geometry.cu ----
-void moments_f64(Geom& g, const double2* sigma, const int* done);
+// component moments (lambda_x, lambda_y, xi, s0) of sigma into `out`
+// (default: the handle's buffer)
+void moments_f64(Geom& g, const double2* sigma, const int* done, double4_32a* out = nullptr);
 
 // ---- dlp_f64.cu ----
 // y = A sigma on the boundary (boundary=true, targets = nodes), or the
 // interior velocity at T targets (boundary=false). All pointers device.
 void dlp_apply_f64(Geom& g, const double2* sigma, double2* y, bool boundary,
                    const double2* targets, int64_t T, const int* done);
+
+// pair kernels alone (into g.part; returns the number of source splits)
+int pairs_f64(Geom& g, const double2* sigma, const double2* targets, int64_t T, bool boundary, PairShape sh,
+              const int* done);
+int pairs_f32(Geom& g, const double2* sigma, const double2* targets, int64_t T, PairShape sh, const int* done);
+int pairs_df64(Geom& g, const double2* sigma, const double2* targets, int64_t T, PairShape sh, const int* done);
+// compiled shape variants of each pair kernel (entry 0 = default); returns the count
+int pair_variants_f64(PairVariant* out, int cap);
+int pair_variants_f32(PairVariant* out, int cap);
+int pair_variants_df64(PairVariant* out, int cap);
+
+// ---- tune.cu ----
+// The launch shape of the pair kernel of `precision` for T targets on this
+// handle: the handle's own choice, else the process-wide tuning cache entry
+// of its size class, else the default.
+PairShape pair_shape(const Geom& g, int precision, int64_t T);
 
 // ---- dlp_f32.cu / dlp_df64.cu ----
 void dlp_apply_f32(Geom& g, const double2* sigma, double2* y, bool boundary,
@@ -276,4 +310,22 @@ SolveResult gmres_solve(Geom& g, const double* f, double* x, double tol, int res
 // operator dispatch used by the solver and the API
 void apply_operator(Geom& g, const double* sigma, double* y, int precision, const int* done);
 
+// ---- batch.cu ----
+// y[k R + r] = A_k sigma[k R + r] for geometries k and right-hand sides r < R
+// (device arrays), FP32 or DF64, one persistent pair launch.
+void batch_matvec(Geom* const* geoms, int n_geoms, int R, const double* const* sigma, double* const* y,
+                  int precision);
+// lockstep flexible GMRES of all (geometry, right-hand side) systems
+void batch_solve(Geom* const* geoms, int n_geoms, int R, const double* const* f, double tol, int restart,
+                 int max_iter, int precision, double* const* sigma, int* iters, double* relres, int* status);
+
+// ---- api.cu ----
+// runs fn(ctx), mapping exceptions to a status code and the thread's last error
+int guarded_call(void (*fn)(void*), void* ctx);
+
 }  // namespace stokes
+
+// the opaque handle of the C ABI
+struct stokes_geom {
+  stokes::Geom* g;
+};

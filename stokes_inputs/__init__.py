@@ -386,6 +386,17 @@ def batch_geometry(index: int, n_pores=None, n_per_pore=None, n_outer=None):
                   {"name": f"batch{index}"})
 
 
+def batch_small_geometry(index: int):
+    """A geometry of the scaled-down uneven batch: pore count uniform in
+    [20, 120], 64 or 128 nodes per pore, 1024 or 2048 wall nodes, otherwise
+    as batch_geometry. Seed = index."""
+    rng = np.random.default_rng(20_000 + index)
+    M = int(rng.integers(20, 121))
+    npp = int(rng.choice([64, 128]))
+    no = int(rng.choice([1024, 2048]))
+    return batch_geometry(index, n_pores=M, n_per_pore=npp, n_outer=no)
+
+
 # ---------------------------------------------------------------------------
 # Boundary data (rows of f, shape (N, 2))
 # ---------------------------------------------------------------------------
@@ -531,8 +542,8 @@ def _source_tag() -> str:
 
 
 def cached_geometry(name: str, seed: int = 0, cache_dir=None) -> Geometry:
-    """config1_geometry / config2_geometry / batch_geometry by name
-    ("cfg1", "cfg2", "batch<i>"), stored as .npz under `cache_dir`
+    """config1_geometry / config2_geometry / batch_geometry /
+    batch_small_geometry by name ("cfg1", "cfg2", "batch<i>", "batchsmall<i>"), stored as .npz under `cache_dir`
     (default: <repo>/.cache) keyed by the generator's source hash."""
     import os
     import pathlib
@@ -550,6 +561,8 @@ def cached_geometry(name: str, seed: int = 0, cache_dir=None) -> Geometry:
         g = config1_geometry(seed)
     elif name == "cfg2":
         g = config2_geometry(seed)
+    elif name.startswith("batchsmall"):
+        g = batch_small_geometry(int(name[10:]))
     elif name.startswith("batch"):
         g = batch_geometry(int(name[5:]))
     else:
