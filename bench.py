@@ -62,6 +62,7 @@ def parse_args():
     p.add_argument("--targets", type=int, default=4096)
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-tune", action="store_true", help="skip the pair kernels' launch-shape autotuner")
     p.add_argument("--kernel-bench", action="store_true",
                    help="time only operator applications (A sigma) of each precision on the workload")
     p.add_argument("--batch-bench", action="store_true",
@@ -407,6 +408,23 @@ def main():
         finally:
             S.stokes_geometry_destroy(h)
 
+    # launch shapes of the pair kernels this solve uses, tuned once for the
+    # workload's size class (kept in the library's process-wide cache)
+    tuned = {}
+    if not args.no_tune:
+        h = S.stokes_geometry_create(nodes, normals, weights, curv, geom.offsets, geom.n_comp, geom.outer_comp,
+                                     centres, sptr)
+        try:
+            for name, p in (("fp32", S.STOKES_FP32), ("df64", S.STOKES_DF64)):
+                if prec_name in ("mixed",) and name == "df64":
+                    continue
+                if prec_name == "fp64":
+                    continue
+                v, c, ms = S.stokes_autotune(h, p, 2)
+                tuned[name] = {"variant": v, "shape": S.stokes_pair_shape_info(p, v), "ctas_per_sm": c,
+                               "ms": round(ms, 3)}
+        finally:
+            S.stokes_geometry_destroy(h)
     # warm-up
     for _ in range(args.warmup):
         run_step()
@@ -489,6 +507,7 @@ def main():
                 "pc": {"bd": "block-diagonal (right)",
                        "twogrid": f"two-grid, coarse = every {args.coarsen}th node (flexible GMRES, right)"}[pc_name],
                 "l2": "working set (block inverses and factors > 2.6 GB, Krylov basis) exceeds L2; no flush",
+                "pair_shapes": tuned or "defaults",
                 "parallelism": f"replicas x{world}"})
     value = ms_step / 1e3
     line = {"metric": METRIC, "value": round(value, 4), "unit": "s", "n_gpus": world, "steps": args.steps,

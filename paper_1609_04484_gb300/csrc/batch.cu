@@ -575,7 +575,8 @@ bool is_device_pointer(const void* p);
 struct Batch {
   std::vector<Geom*> gs;
   int R = 0, S = 0, m = 0;
-  cudaStream_t s = nullptr;
+  cudaStream_t s = nullptr;   // the handles' stream
+  cudaStream_t ls = nullptr;  // stream the batched launches go to (s, or the capture stream)
   // operator
   std::vector<BGeom> tab;
   DevBuf<BGeom> d_tab;
@@ -651,6 +652,7 @@ void batch_init(Batch& b, Geom* const* geoms, int n_geoms, int R) {
   b.R = R;
   b.S = n_geoms * R;
   b.s = b.gs[0]->stream;
+  b.ls = b.s;
   for (Geom* g : b.gs) {
     require(g != nullptr, "null handle");
     require(g->stream == b.s, "all handles of a batch must use the same stream");
@@ -677,12 +679,12 @@ void batch_apply(Batch& b, int precision, int col, const std::vector<const doubl
       moments_f64(g, (const double2*)sg, done_sys.empty() ? nullptr : done_sys[sidx], b.mom.get() + b.mom_off[sidx]);
     }
   }
-  STOKES_CUDA(cudaMemsetAsync(b.counter.get(), 0, sizeof(unsigned long long), b.s));
+  STOKES_CUDA(cudaMemsetAsync(b.counter.get(), 0, sizeof(unsigned long long), b.ls));
   switch (R) {
-    case 1: launch_pairs_r<1>(precision, b.d_tab.get(), n_geoms, b.n_items, col, b.counter.get(), all_done, b.s); break;
-    case 2: launch_pairs_r<2>(precision, b.d_tab.get(), n_geoms, b.n_items, col, b.counter.get(), all_done, b.s); break;
-    case 3: launch_pairs_r<3>(precision, b.d_tab.get(), n_geoms, b.n_items, col, b.counter.get(), all_done, b.s); break;
-    default: launch_pairs_r<4>(precision, b.d_tab.get(), n_geoms, b.n_items, col, b.counter.get(), all_done, b.s);
+    case 1: launch_pairs_r<1>(precision, b.d_tab.get(), n_geoms, b.n_items, col, b.counter.get(), all_done, b.ls); break;
+    case 2: launch_pairs_r<2>(precision, b.d_tab.get(), n_geoms, b.n_items, col, b.counter.get(), all_done, b.ls); break;
+    case 3: launch_pairs_r<3>(precision, b.d_tab.get(), n_geoms, b.n_items, col, b.counter.get(), all_done, b.ls); break;
+    default: launch_pairs_r<4>(precision, b.d_tab.get(), n_geoms, b.n_items, col, b.counter.get(), all_done, b.ls);
   }
   for (int k = 0; k < n_geoms; ++k) {
     Geom& g = *b.gs[k];
@@ -792,31 +794,35 @@ void batch_cycle_launches(Batch& b, int precision) {
         precond_apply(g, Sy.V + (int64_t)j * Sy.n, Sy.Z + (int64_t)j * Sy.n, Sy.state, f32pc);
       else
         STOKES_CUDA(cudaMemcpyAsync(Sy.Z + (int64_t)j * Sy.n, Sy.V + (int64_t)j * Sy.n, Sy.n * sizeof(double),
-                                    cudaMemcpyDeviceToDevice, b.s));
+                                    cudaMemcpyDeviceToDevice, b.ls));
     }
     batch_apply(b, precision, j, zbase, 1, wout, done, b.all_done.get());
     for (int pass = 0; pass < 2; ++pass) {
-      kb_dot_partial<<<dim3(nblk, S), 256, 0, b.s>>>(b.d_sys.get(), j, m);
-      kb_reduce<<<dim3((unsigned)((j + 1 + 255) / 256), S), 256, 0, b.s>>>(b.d_sys.get(), j, m, pass);
-      kb_orth_update<<<dim3(nblk, S), 256, 0, b.s>>>(b.d_sys.get(), j, pass);
+      kb_dot_partial<<<dim3(nblk, S), 256, 0, b.ls>>>(b.d_sys.get(), j, m);
+      kb_reduce<<<dim3((unsigned)((j + 1 + 255) / 256), S), 256, 0, b.ls>>>(b.d_sys.get(), j, m, pass);
+      kb_orth_update<<<dim3(nblk, S), 256, 0, b.ls>>>(b.d_sys.get(), j, pass);
     }
-    kb_finish<<<1, ((S + 31) / 32) * 32, 0, b.s>>>(b.d_sys.get(), S, j, m, b.all_done.get(), b.est.get());
-    kb_scale_next<<<dim3(std::min<unsigned>(64, (unsigned)((b.max_n + 255) / 256)), S), 256, 0, b.s>>>(
+    kb_finish<<<1, ((S + 31) / 32) * 32, 0, b.ls>>>(b.d_sys.get(), S, j, m, b.all_done.get(), b.est.get());
+    kb_scale_next<<<dim3(std::min<unsigned>(64, (unsigned)((b.max_n + 255) / 256)), S), 256, 0, b.ls>>>(
         b.d_sys.get(), j);
     STOKES_LAUNCHED();
   }
-  kb_lsq<<<S, 256, 0, b.s>>>(b.d_sys.get(), m);
-  kb_update<<<dim3(std::min<unsigned>(64, (unsigned)((b.max_n + 255) / 256)), S), 256, 0, b.s>>>(b.d_sys.get());
+  kb_lsq<<<S, 256, 0, b.ls>>>(b.d_sys.get(), m);
+  kb_update<<<dim3(std::min<unsigned>(64, (unsigned)((b.max_n + 255) / 256)), S), 256, 0, b.ls>>>(b.d_sys.get());
   STOKES_LAUNCHED();
 }
 
 // True residuals r = f - A x (FP64 operator per system) and their norms.
-void batch_residuals(Batch& b, const std::vector<const double*>& f, bool x_zero, std::vector<double>& rn) {
+// Systems with active[s] == 0 keep rn[s] (their r is not needed again).
+void batch_residuals(Batch& b, const std::vector<const double*>& f, bool x_zero, std::vector<double>& rn,
+                     const std::vector<int>* active = nullptr) {
   const int S = b.S;
   std::vector<const double*> th(S);
+  const std::vector<double> keep = rn;
   for (int sidx = 0; sidx < S; ++sidx) {
     th[sidx] = b.t_h[sidx];
-    if (!x_zero) apply_operator(*b.gs[sidx / b.R], b.sys[sidx].x, b.t_h[sidx], STOKES_FP64, nullptr);
+    const bool act = !active || (*active)[sidx];
+    if (!x_zero && act) apply_operator(*b.gs[sidx / b.R], b.sys[sidx].x, b.t_h[sidx], STOKES_FP64, nullptr);
   }
   STOKES_CUDA(cudaMemcpyAsync(b.d_f.get(), f.data(), S * sizeof(double*), cudaMemcpyHostToDevice, b.s));
   STOKES_CUDA(cudaMemcpyAsync(b.d_t.get(), th.data(), S * sizeof(double*), cudaMemcpyHostToDevice, b.s));
@@ -827,6 +833,9 @@ void batch_residuals(Batch& b, const std::vector<const double*>& f, bool x_zero,
   rn.resize(S);
   STOKES_CUDA(cudaMemcpyAsync(rn.data(), b.norms.get(), S * sizeof(double), cudaMemcpyDeviceToHost, b.s));
   STOKES_CUDA(cudaStreamSynchronize(b.s));
+  if (active)
+    for (int sidx = 0; sidx < S; ++sidx)
+      if (!(*active)[sidx] && sidx < (int)keep.size()) rn[sidx] = keep[sidx];
 }
 
 }  // namespace
@@ -854,17 +863,37 @@ static void batch_fgmres(Batch& b, int precision, const std::vector<const double
     STOKES_LAUNCHED();
     batch_cycle_launches(b, precision);
     STOKES_CUDA(cudaStreamSynchronize(b.s));
-    cudaGraph_t graph;
-    STOKES_CUDA(cudaStreamBeginCapture(b.s, cudaStreamCaptureModeThreadLocal));
-    try {
-      batch_cycle_launches(b, precision);
-    } catch (...) {
-      cudaGraph_t dummy;
-      cudaStreamEndCapture(b.s, &dummy);
-      if (dummy) cudaGraphDestroy(dummy);
-      throw;
+    // The handles' stream may be the legacy default stream, which cannot be
+    // captured: every launch of the cycle (the per-geometry ones included)
+    // is recorded on a private stream; the graph then runs on the handles' stream.
+    struct CaptureStreams {
+      Batch& b;
+      cudaStream_t cs = nullptr;
+      explicit CaptureStreams(Batch& bb) : b(bb) {
+        STOKES_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        b.ls = cs;
+        for (Geom* g : b.gs) g->stream = cs;
+      }
+      ~CaptureStreams() {
+        for (Geom* g : b.gs) g->stream = b.s;
+        b.ls = b.s;
+        if (cs) cudaStreamDestroy(cs);
+      }
+    };
+    cudaGraph_t graph = nullptr;
+    {
+      CaptureStreams cap(b);
+      STOKES_CUDA(cudaStreamBeginCapture(cap.cs, cudaStreamCaptureModeThreadLocal));
+      try {
+        batch_cycle_launches(b, precision);
+      } catch (...) {
+        cudaGraph_t dummy = nullptr;
+        cudaStreamEndCapture(cap.cs, &dummy);
+        if (dummy) cudaGraphDestroy(dummy);
+        throw;
+      }
+      STOKES_CUDA(cudaStreamEndCapture(cap.cs, &graph));
     }
-    STOKES_CUDA(cudaStreamEndCapture(b.s, &graph));
     const cudaError_t e = cudaGraphInstantiate(&b.cycle, graph, 0);
     cudaGraphDestroy(graph);
     STOKES_CUDA(e);
@@ -877,7 +906,8 @@ static void batch_fgmres(Batch& b, int precision, const std::vector<const double
   std::vector<int> live(S, 0), met(S, 0), hstate(4 * S);
   std::vector<double> scal_init(8, 0.0);
   for (int cyc = 0;; ++cyc) {
-    batch_residuals(b, f, x_zero && cyc == 0, rn);
+    // after the first cycle only the systems that iterated need a new residual
+    batch_residuals(b, f, x_zero && cyc == 0, rn, cyc == 0 ? nullptr : &live);
     int n_live = 0;
     for (int sidx = 0; sidx < S; ++sidx) {
       relres[sidx] = fnorm[sidx] > 0 ? rn[sidx] / fnorm[sidx] : 0.0;
