@@ -70,6 +70,8 @@ def parse_args():
     p.add_argument("--batch-geoms", type=int, default=16)
     p.add_argument("--reps", type=int, default=5)
     p.add_argument("--precisions", default="fp32,df64,fp64")
+    p.add_argument("--shape", default="",
+                   help="kernel-bench launch shapes, e.g. df64:2:4,fp32:4:8 (precision:variant:ctas_per_sm)")
     return p.parse_args()
 
 
@@ -228,6 +230,11 @@ def kernel_bench(args):
     kinds = {"fp32": (S.STOKES_FP32, S.STOKES_PROF_PAIRS_FP32, "k_dlp_pairs_f32"),
              "df64": (S.STOKES_DF64, S.STOKES_PROF_PAIRS_DF64, "k_dlp_pairs_df64"),
              "fp64": (S.STOKES_FP64, S.STOKES_PROF_PAIRS_FP64, "k_dlp_pairs_f64")}
+    shapes = {}
+    for item in filter(None, args.shape.split(",")):
+        name, v, c = item.split(":")
+        S.stokes_set_pair_shape(G.handle, kinds[name][0], int(v), int(c))
+        shapes[name] = (int(v), int(c))
     for name in args.precisions.split(","):
         prec, kind, kname = kinds[name]
         for _ in range(args.warmup):
@@ -245,7 +252,10 @@ def kernel_bench(args):
         S.stokes_profile_enable(G.handle, False)
         avg = ms / n
         gp = pairs / n / (avg * 1e-3)
+        v, c = S.stokes_get_pair_shape(G.handle, prec, geom.n_nodes)
         print(json.dumps({"kernel": kname, "precision": name, "workload": workload_config(args.workload)["workload"],
+                          "shape": {"variant": v, "threads_tpt_tile": S.stokes_pair_shape_info(prec, v),
+                                    "ctas_per_sm": c},
                           "matvec_ms": round(ev0.elapsed_time(ev1) / args.reps, 3),
                           "pair_kernel_ms": round(avg, 3), "epilogue_ms": round(mse / max(ne, 1), 3),
                           "gpairs_per_s": round(gp / 1e9, 1),
@@ -276,7 +286,7 @@ def batch_bench(args):
     Gs = [S.Geometry(g, stream=stream.cuda_stream) for g in geoms]
     hs = [G.handle for G in Gs]
     for G in Gs:
-        S.stokes_precond_setup(G.handle, S.STOKES_PC_BLOCKDIAG)
+        S.stokes_precond_setup_twogrid(G.handle, args.coarsen)
     sig = [torch.tensor(si.random_density(g, r).reshape(-1), device=dev) for g in geoms for r in range(R)]
     ys = [torch.empty_like(x) for x in sig]
     pairs = float(sum(g.n_nodes ** 2 for g in geoms)) * R
@@ -313,7 +323,7 @@ def batch_bench(args):
         xs = [torch.zeros_like(f) for f in fs]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        iters, relres, status = S.stokes_batch_solve(hs, R, fs, xs, tol=args.tol, restart=50, max_iter=3000,
+        iters, relres, status = S.stokes_batch_solve(hs, R, fs, xs, tol=args.tol, restart=100, max_iter=3000,
                                                      precision=S.STOKES_MIXED_IR)
         torch.cuda.synchronize()
         t_batch = time.perf_counter() - t0
@@ -322,12 +332,12 @@ def batch_bench(args):
     for k, G in enumerate(Gs):
         for r in range(R):
             x1 = torch.zeros_like(fs[k * R + r])
-            code, it, rr, _ = S.stokes_gmres_solve(G.handle, fs[k * R + r], x1, tol=args.tol, restart=50,
+            code, it, rr, _ = S.stokes_gmres_solve(G.handle, fs[k * R + r], x1, tol=args.tol, restart=100,
                                                    max_iter=3000, precision=S.STOKES_MIXED_IR)
             it_single.append(it)
     torch.cuda.synchronize()
     t_single = time.perf_counter() - t0
-    print(json.dumps({"batch_solve": "mixed (FP32 inner, FP64 outer), block diagonal, FGMRES(50)",
+    print(json.dumps({"batch_solve": f"mixed (FP32 inner, FP64 outer), two-grid (q = {args.coarsen}), FGMRES(100)",
                       "config": cfg["workload"], "systems": len(fs), "tol": args.tol,
                       "batch_s": round(t_batch, 3), "one_solve_per_system_s": round(t_single, 3),
                       "speedup": round(t_single / t_batch, 2), "iters_max": max(iters),

@@ -176,6 +176,7 @@ struct TwoGrid {
   DevBuf<int> piv, perm, status;
   DevBuf<double> rc, zc, h;
   DevBuf<float> rc32;
+  DevBuf<float> gemv_part;         // column-split partial sums of the coarse apply
   DevBuf<float> work32;
   DevBuf<int> d_pore_ids;
 };

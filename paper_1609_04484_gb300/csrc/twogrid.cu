@@ -149,35 +149,40 @@ k_coarse_assemble(int64_t Nc, const float4* __restrict__ P, const float4* __rest
   }
 }
 
-// y = X x for a dense column-major float matrix: CTA per 256 rows; thread t
-// of 256 owns rows 4 (t mod 64) .. + 3 (one float4 per column) and the
-// columns q = t / 64 (mod 4); partial sums are combined in shared memory.
+// y = X x for a dense column-major float m x m matrix, in two passes.
+// Pass 1: CTA (b, c) covers rows [1024 b, 1024 b + 1024) (four consecutive
+// rows per thread, one float4 per column: each warp reads 512 contiguous
+// bytes of a column) and the column range [c w, c w + w); its partial sums go
+// to part[c][rows]. A grid of (m / 1024) x kGemvSplits CTAs keeps several
+// CTAs per SM streaming the matrix. Pass 2 adds the kGemvSplits partials in a
+// fixed order (deterministic) and writes y in double.
+constexpr int kGemvSplits = 32;
+
 __global__ void __launch_bounds__(256)
-k_dense_gemv32(const float* __restrict__ X, int64_t m, const float* __restrict__ x, double* __restrict__ y,
-               const int* __restrict__ done) {
+k_dense_gemv32_part(const float* __restrict__ X, int64_t m, const float* __restrict__ x, float* __restrict__ part,
+                    const int* __restrict__ done) {
   count_launch();
   if (done && *done) return;
-  __shared__ float4 red[4][64];
-  const int64_t r0 = blockIdx.x * (int64_t)256;
-  const int tr = threadIdx.x & 63, ph = threadIdx.x >> 6;
-  const int64_t r = r0 + 4 * tr;
+  const int64_t r = blockIdx.x * (int64_t)1024 + 4 * (int64_t)threadIdx.x;
+  const int64_t w = (m + kGemvSplits - 1) / kGemvSplits;
+  const int64_t q0 = blockIdx.y * w, q1 = imin64(m, q0 + w);
   float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
-  if ((m & 3) == 0 && r + 3 < m) {  // float4 loads need 16-byte aligned rows
-    int64_t q = ph;
-    for (; q + 4 < m; q += 8) {
+  if ((m & 3) == 0 && r + 3 < m) {  // float4 loads need 16-byte aligned columns
+    int64_t q = q0;
+    for (; q + 1 < q1; q += 2) {
       const float4 u = *reinterpret_cast<const float4*>(X + q * m + r);
-      const float4 v = *reinterpret_cast<const float4*>(X + (q + 4) * m + r);
-      const float xu = x[q], xv = x[q + 4];
+      const float4 v = *reinterpret_cast<const float4*>(X + (q + 1) * m + r);
+      const float xu = x[q], xv = x[q + 1];
       a0.x = fmaf(u.x, xu, a0.x); a0.y = fmaf(u.y, xu, a0.y); a0.z = fmaf(u.z, xu, a0.z); a0.w = fmaf(u.w, xu, a0.w);
       a1.x = fmaf(v.x, xv, a1.x); a1.y = fmaf(v.y, xv, a1.y); a1.z = fmaf(v.z, xv, a1.z); a1.w = fmaf(v.w, xv, a1.w);
     }
-    for (; q < m; q += 4) {
+    if (q < q1) {
       const float4 u = *reinterpret_cast<const float4*>(X + q * m + r);
       const float xu = x[q];
       a0.x = fmaf(u.x, xu, a0.x); a0.y = fmaf(u.y, xu, a0.y); a0.z = fmaf(u.z, xu, a0.z); a0.w = fmaf(u.w, xu, a0.w);
     }
   } else if (r < m) {
-    for (int64_t q = ph; q < m; q += 4) {
+    for (int64_t q = q0; q < q1; ++q) {
       const float xu = x[q];
       const float* col = X + q * m + r;
       a0.x = fmaf(col[0], xu, a0.x);
@@ -186,14 +191,20 @@ k_dense_gemv32(const float* __restrict__ X, int64_t m, const float* __restrict__
       if (r + 3 < m) a0.w = fmaf(col[3], xu, a0.w);
     }
   }
-  red[ph][tr] = make_float4(a0.x + a1.x, a0.y + a1.y, a0.z + a1.z, a0.w + a1.w);
-  __syncthreads();
-  if (ph == 0) {
-    const float4 s0 = red[0][tr], s1 = red[1][tr], s2 = red[2][tr], s3 = red[3][tr];
-    const float o[4] = {(s0.x + s1.x) + (s2.x + s3.x), (s0.y + s1.y) + (s2.y + s3.y),
-                        (s0.z + s1.z) + (s2.z + s3.z), (s0.w + s1.w) + (s2.w + s3.w)};
-    for (int c = 0; c < 4; ++c)
-      if (r + c < m) y[r + c] = (double)o[c];
+  float* out = part + blockIdx.y * m;
+  const float o[4] = {a0.x + a1.x, a0.y + a1.y, a0.z + a1.z, a0.w + a1.w};
+  for (int c = 0; c < 4; ++c)
+    if (r + c < m) out[r + c] = o[c];
+}
+
+__global__ void k_dense_gemv32_sum(const float* __restrict__ part, int64_t m, double* __restrict__ y,
+                                   const int* __restrict__ done) {
+  count_launch();
+  if (done && *done) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int c = 0; c < kGemvSplits; ++c) s += part[c * m + i];
+    y[i] = (double)s;
   }
 }
 
@@ -578,6 +589,7 @@ void twogrid_setup(Geom& g, int q) {
   t.rc.alloc(m);
   t.rc32.alloc(m);
   t.zc.alloc(m);
+  t.gemv_part.alloc((size_t)kGemvSplits * m);
   t.h.alloc(2 * g.N);
   // explicit float inverse of the coarse operator: each apply is then one
   // memory-bound matrix-vector product
@@ -603,7 +615,10 @@ static void twogrid_apply(Geom& g, const double* r, double* z, const int* done, 
                                 t.rc32.get(), done);
   STOKES_LAUNCHED();
   const int64_t m = 2 * t.Nc;
-  k_dense_gemv32<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(t.inv.get(), m, t.rc32.get(), t.zc.get(), done);
+  k_dense_gemv32_part<<<dim3((unsigned)((m + 1023) / 1024), kGemvSplits), 256, 0, s>>>(t.inv.get(), m, t.rc32.get(),
+                                                                                     t.gemv_part.get(), done);
+  k_dense_gemv32_sum<<<(unsigned)std::min<int64_t>(152 * 4, (m + 255) / 256), 256, 0, s>>>(t.gemv_part.get(), m,
+                                                                                         t.zc.get(), done);
   STOKES_LAUNCHED();
   dim3 gp((unsigned)std::min<int64_t>(64, nmax), (unsigned)nc);
   k_prolong<<<gp, 128, 0, s>>>(nc, g.outer, g.d_off.get(), t.d_off_c.get(), t.d_ioff.get(), t.interp.get(), r,

@@ -105,8 +105,8 @@ def test_batch_matvec_matches_oracle(S, gpu, prec, bound, R):
 def test_batch_solve_matches_dense_oracle(S, gpu, prec):
     """4 geometries x 4 right-hand sides (pipe, reversed pipe, wall shear,
     Stokeslet/rotlet data): every density equals the dense LU solution; the
-    outer-only geometry runs without a preconditioner, the others with their
-    block diagonal."""
+    outer-only geometry runs without a preconditioner, the 1152-node pipe
+    with the two-grid one, the others with their block diagonal."""
     torch = gpu
     dev = torch.device("cuda:0")
     geoms = _geoms()
@@ -114,7 +114,9 @@ def test_batch_solve_matches_dense_oracle(S, gpu, prec):
     Gs = [S.Geometry(g) for g in geoms]
     try:
         for k, G in enumerate(Gs):
-            if geoms[k].n_pores:
+            if k == 3:
+                S.stokes_precond_setup_twogrid(G.handle, 4)
+            elif geoms[k].n_pores:
                 S.stokes_precond_setup(G.handle, S.STOKES_PC_BLOCKDIAG)
         fs, xs, refs = [], [], []
         for g in geoms:
