@@ -279,9 +279,14 @@ def batch_bench(args):
     import torch
     import paper_1609_04484_gb300 as S
     import stokes_inputs as si
-    dev = torch.device("cuda", 0)
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     geoms = batch_workload(args.batch_geoms)
+    if world > 1:  # independent geometries: each rank solves its share, no collective on the data path
+        from paper_1609_04484_gb300.replicas import shard_by_cost
+        geoms = [geoms[i] for i in shard_by_cost([g.n_nodes ** 2 for g in geoms], world, rank)]
     R = 4
     Gs = [S.Geometry(g, stream=stream.cuda_stream) for g in geoms]
     hs = [G.handle for G in Gs]
@@ -458,9 +463,8 @@ def main():
     launches = S.stokes_kernel_launches() - launches0
     ms_step = ev0.elapsed_time(ev1) / args.steps
     if pg is not None:
-        t = torch.tensor([ms_step], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms_step = float(t.item())
+        from paper_1609_04484_gb300.replicas import reduce_max
+        ms_step = reduce_max(ms_step, device=dev)
 
     # end to end through the public API with host (pinned) buffers
     pin = lambda a: torch.tensor(np.ascontiguousarray(a).reshape(-1), dtype=torch.float64).pin_memory()

@@ -21,55 +21,112 @@ namespace {
 
 constexpr int kTs = 64;
 
-// C = alpha A B + beta C (column-major, M x N = (M x K)(K x N)): 128 x 128
-// output tile per CTA, 8 x 8 per thread, operands staged 16 deep.
+// C = alpha A B + beta C for column-major float matrices. CTA: a 128 x 128
+// tile of C, 256 threads, 8 x 8 outputs per thread (rows 4 tx .. 4 tx + 3 and
+// 64 + 4 tx .., columns 4 ty .. and 64 + 4 ty ..), so each k step reads two
+// float4 of A and two of B from shared memory for 64 FMAs. K advances by 8;
+// the next step's tiles are loaded into registers while the current one is
+// computed, then stored to the other shared-memory buffer (double
+// buffering). kVec: leading dimensions multiples of 4 and 16-byte aligned
+// bases, so interior tiles move as float4.
+template <bool kVec>
 __global__ void __launch_bounds__(256)
-k_sgemm(int64_t M, int64_t N, int K, float alpha, const float* __restrict__ A, int64_t lda,
-        const float* __restrict__ B, int64_t ldb, float beta, float* __restrict__ C, int64_t ldc) {
+k_sgemm128(int64_t M, int64_t N, int K, float alpha, const float* __restrict__ A, int64_t lda,
+           const float* __restrict__ B, int64_t ldb, float beta, float* __restrict__ C, int64_t ldc) {
   count_launch();
-  constexpr int kK = 16, kT = 128;
-  __shared__ float sA[kK][kT + 4];  // [k][row]
-  __shared__ float sB[kK][kT + 4];  // [k][col]
-  const int64_t r0 = blockIdx.x * (int64_t)kT, c0 = blockIdx.y * (int64_t)kT;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  float acc[8][8] = {};
-  for (int k0 = 0; k0 < K; k0 += kK) {
-    __syncthreads();
-    for (int e = threadIdx.x; e < kK * kT; e += 256) {
-      const int kk = e / kT, rr = e % kT;
-      const int64_t r = r0 + rr;
-      sA[kk][rr] = (k0 + kk < K && r < M) ? A[(int64_t)(k0 + kk) * lda + r] : 0.f;
+  __shared__ __align__(16) float sA[2][8][128];  // [buffer][k][row]
+  __shared__ __align__(16) float sB[2][8][128];  // [buffer][k][column]
+  const int t = threadIdx.x;
+  const int64_t r0 = blockIdx.x * (int64_t)128, c0 = blockIdx.y * (int64_t)128;
+  const int la_k = t >> 5, la_r = (t & 31) * 4;  // A loader: one k, four rows
+  const int lb_c = t >> 1, lb_k = (t & 1) * 4;   // B loader: one column, four k
+  float4 ra, rb;
+  auto load = [&](int k0) {
+    const int64_t r = r0 + la_r;
+    const int ka = k0 + la_k;
+    if (kVec && ka < K && r + 3 < M) {
+      ra = *reinterpret_cast<const float4*>(A + (int64_t)ka * lda + r);
+    } else {
+      const float* col = A + (int64_t)ka * lda;
+      ra.x = (ka < K && r < M) ? col[r] : 0.f;
+      ra.y = (ka < K && r + 1 < M) ? col[r + 1] : 0.f;
+      ra.z = (ka < K && r + 2 < M) ? col[r + 2] : 0.f;
+      ra.w = (ka < K && r + 3 < M) ? col[r + 3] : 0.f;
     }
-    for (int e = threadIdx.x; e < kK * kT; e += 256) {
-      const int cc = e / kK, kk = e % kK;
-      const int64_t c = c0 + cc;
-      sB[kk][cc] = (k0 + kk < K && c < N) ? B[c * ldb + k0 + kk] : 0.f;
+    const int64_t c = c0 + lb_c;
+    const int kb = k0 + lb_k;
+    if (kVec && c < N && kb + 3 < K) {
+      rb = *reinterpret_cast<const float4*>(B + c * ldb + kb);
+    } else {
+      const float* col = B + c * ldb;
+      rb.x = (c < N && kb < K) ? col[kb] : 0.f;
+      rb.y = (c < N && kb + 1 < K) ? col[kb + 1] : 0.f;
+      rb.z = (c < N && kb + 2 < K) ? col[kb + 2] : 0.f;
+      rb.w = (c < N && kb + 3 < K) ? col[kb + 3] : 0.f;
     }
-    __syncthreads();
+  };
+  auto store = [&](int buf) {
+    *reinterpret_cast<float4*>(&sA[buf][la_k][la_r]) = ra;
+    sB[buf][lb_k][lb_c] = rb.x;
+    sB[buf][lb_k + 1][lb_c] = rb.y;
+    sB[buf][lb_k + 2][lb_c] = rb.z;
+    sB[buf][lb_k + 3][lb_c] = rb.w;
+  };
+  const int tx = t & 15, ty = t >> 4;
+  float acc[8][8];
 #pragma unroll
-    for (int kk = 0; kk < kK; ++kk) {
-      float a[8], b[8];
+  for (int p = 0; p < 8; ++p)
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        a[q] = sA[kk][tx + 16 * q];
-        b[q] = sB[kk][ty + 16 * q];
-      }
+    for (int q = 0; q < 8; ++q) acc[p][q] = 0.f;
+  load(0);
+  store(0);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < K; k0 += 8) {
+    const bool more = k0 + 8 < K;
+    if (more) load(k0 + 8);
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&sA[buf][kk][4 * tx]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&sA[buf][kk][64 + 4 * tx]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&sB[buf][kk][4 * ty]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&sB[buf][kk][64 + 4 * ty]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
       for (int p = 0; p < 8; ++p)
 #pragma unroll
         for (int q = 0; q < 8; ++q) acc[p][q] = fmaf(a[p], b[q], acc[p][q]);
     }
+    if (more) {
+      store(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
   }
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    const int64_t c = c0 + ty + 16 * q;
+    const int64_t c = c0 + (q < 4 ? 4 * ty + q : 64 + 4 * ty + q - 4);
     if (c >= N) continue;
 #pragma unroll
-    for (int p = 0; p < 8; ++p) {
-      const int64_t r = r0 + tx + 16 * p;
-      if (r < M) {
-        float* cp = C + c * ldc + r;
-        *cp = beta == 0.f ? alpha * acc[p][q] : fmaf(alpha, acc[p][q], beta * *cp);
+    for (int h = 0; h < 2; ++h) {
+      const int64_t r = r0 + 64 * h + 4 * tx;
+      float* cp = C + c * ldc + r;
+      const float v[4] = {alpha * acc[4 * h][q], alpha * acc[4 * h + 1][q], alpha * acc[4 * h + 2][q],
+                          alpha * acc[4 * h + 3][q]};
+      if (kVec && r + 3 < M) {
+        float4 o = make_float4(v[0], v[1], v[2], v[3]);
+        if (beta != 0.f) {
+          const float4 old = *reinterpret_cast<const float4*>(cp);
+          o.x = fmaf(beta, old.x, o.x);
+          o.y = fmaf(beta, old.y, o.y);
+          o.z = fmaf(beta, old.z, o.z);
+          o.w = fmaf(beta, old.w, o.w);
+        }
+        *reinterpret_cast<float4*>(cp) = o;
+      } else {
+        for (int i = 0; i < 4; ++i)
+          if (r + i < M) cp[i] = beta == 0.f ? v[i] : fmaf(beta, cp[i], v[i]);
       }
     }
   }
@@ -131,14 +188,23 @@ __global__ void k_copy_rows(const float* __restrict__ src, int64_t lds, float* _
   }
 }
 
-void sgemm(cudaStream_t s, int64_t M, int64_t N, int K, float alpha, const float* A, int64_t lda, const float* B,
-           int64_t ldb, float beta, float* C, int64_t ldc) {
+}  // namespace
+
+void sgemm32(cudaStream_t s, int64_t M, int64_t N, int K, float alpha, const float* A, int64_t lda, const float* B,
+             int64_t ldb, float beta, float* C, int64_t ldc) {
   if (M <= 0 || N <= 0) return;
   dim3 grid((unsigned)((M + 127) / 128), (unsigned)((N + 127) / 128));
-  k_sgemm<<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  const bool vec = ((lda | ldb | ldc) & 3) == 0 && ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B) |
+                                                     reinterpret_cast<uintptr_t>(C)) & 15) == 0;
+  if (vec)
+    k_sgemm128<true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  else
+    k_sgemm128<false><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
   STOKES_LAUNCHED();
 }
 
+namespace {
+using stokes::sgemm32;
 }  // namespace
 
 // X (m x m, column-major) = inverse of the block whose float factors are LU
@@ -158,22 +224,22 @@ void invert_from_lu32(Geom& g, const float* LU, int64_t m, const int* perm, floa
   for (int64_t t = 0; t < nt; ++t) {
     const int64_t r0 = t * kTs;
     const int n = (int)imin64(kTs, m - r0);
-    sgemm(s, n, m, n, 1.f, tinvL.get() + t * kTs * kTs, kTs, X + r0, m, 0.f, tmp.get(), kTs);
+    sgemm32(s, n, m, n, 1.f, tinvL.get() + t * kTs * kTs, kTs, X + r0, m, 0.f, tmp.get(), kTs);
     k_copy_rows<<<(unsigned)std::min<int64_t>(((int64_t)n * m + 255) / 256, 152 * 16), 256, 0, s>>>(
         tmp.get(), kTs, X + r0, m, n, m);
     STOKES_LAUNCHED();
     const int64_t below = m - r0 - n;
-    sgemm(s, below, m, n, -1.f, LU + r0 * m + r0 + n, m, X + r0, m, 1.f, X + r0 + n, m);
+    sgemm32(s, below, m, n, -1.f, LU + r0 * m + r0 + n, m, X + r0, m, 1.f, X + r0 + n, m);
   }
   // backward: X_t = inv(U_tt) W_t; earlier rows -= U_ut X_t
   for (int64_t t = nt - 1; t >= 0; --t) {
     const int64_t r0 = t * kTs;
     const int n = (int)imin64(kTs, m - r0);
-    sgemm(s, n, m, n, 1.f, tinvU.get() + t * kTs * kTs, kTs, X + r0, m, 0.f, tmp.get(), kTs);
+    sgemm32(s, n, m, n, 1.f, tinvU.get() + t * kTs * kTs, kTs, X + r0, m, 0.f, tmp.get(), kTs);
     k_copy_rows<<<(unsigned)std::min<int64_t>(((int64_t)n * m + 255) / 256, 152 * 16), 256, 0, s>>>(
         tmp.get(), kTs, X + r0, m, n, m);
     STOKES_LAUNCHED();
-    sgemm(s, r0, m, n, -1.f, LU + r0 * m, m, X + r0, m, 1.f, X, m);
+    sgemm32(s, r0, m, n, -1.f, LU + r0 * m, m, X + r0, m, 1.f, X, m);
   }
   STOKES_CUDA(cudaStreamSynchronize(s));  // scratch buffers go out of scope
 }

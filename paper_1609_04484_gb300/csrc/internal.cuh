@@ -295,6 +295,9 @@ void twogrid_setup(Geom& g, int q);
 // z = P^-1 v with the current preconditioner (two-grid if set up, else block diagonal)
 void precond_apply(Geom& g, const double* v, double* z, const int* done, bool f32);
 void invert_from_lu32(Geom& g, const float* LU, int64_t m, const int* perm, float* X);
+// C = alpha A B + beta C, column-major float (M x K times K x N)
+void sgemm32(cudaStream_t s, int64_t M, int64_t N, int K, float alpha, const float* A, int64_t lda, const float* B,
+             int64_t ldb, float beta, float* C, int64_t ldc);
 template <class T>
 void lu_solve_persistent(Geom& g, const T* A, int64_t m, const int* perm, const double* v, double* z, T* work,
                          const int* done);

@@ -314,57 +314,6 @@ __global__ void k_trsm_row_panel32(float* __restrict__ A, int64_t m, int64_t k0,
     if (c < kb) col[c] = x[c];
 }
 
-// trailing update A22 -= L21 U12: 128 x 128 output tile per CTA, 8 x 8 per
-// thread, operands staged 16 columns / rows at a time.
-__global__ void __launch_bounds__(256)
-k_gemm_trailing32(float* __restrict__ A, int64_t m, int64_t k0, int kb) {
-  count_launch();
-  constexpr int kK = 16, kT = 128;
-  __shared__ float sL[kK][kT + 4];
-  __shared__ float sU[kK][kT + 4];
-  const int64_t base = k0 + kb;
-  const int64_t r0 = base + blockIdx.x * (int64_t)kT, q0 = base + blockIdx.y * (int64_t)kT;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  float acc[8][8] = {};
-  for (int cb = 0; cb < kb; cb += kK) {
-    __syncthreads();
-    for (int e = threadIdx.x; e < kK * kT; e += 256) {
-      const int c = e / kT, rr = e % kT;
-      const int64_t r = r0 + rr;
-      sL[c][rr] = (cb + c < kb && r < m) ? A[(k0 + cb + c) * m + r] : 0.f;
-    }
-    for (int e = threadIdx.x; e < kK * kT; e += 256) {
-      const int qq = e / kK, c = e % kK;
-      const int64_t q = q0 + qq;
-      sU[c][qq] = (cb + c < kb && q < m) ? A[q * m + k0 + cb + c] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int c = 0; c < kK; ++c) {
-      float l[8], u[8];
-#pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        l[a] = sL[c][tx + 16 * a];
-        u[a] = sU[c][ty + 16 * a];
-      }
-#pragma unroll
-      for (int a = 0; a < 8; ++a)
-#pragma unroll
-        for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(l[a], u[b], acc[a][b]);
-    }
-  }
-#pragma unroll
-  for (int b = 0; b < 8; ++b) {
-    const int64_t q = q0 + ty + 16 * b;
-    if (q >= m) continue;
-#pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      const int64_t r = r0 + tx + 16 * a;
-      if (r < m) A[q * m + r] -= acc[a][b];
-    }
-  }
-}
-
 // rc = R r per component (x and y): rc_j = (n_c / n_f) sum_i P[i][j] r_i.
 // Transfers run in single precision (a preconditioner: flexible GMRES
 // absorbs the rounding).
@@ -569,8 +518,9 @@ void twogrid_setup(Geom& g, int q) {
     const int64_t rest = m - k0 - kb;
     if (rest > 0) {
       k_trsm_row_panel32<<<(unsigned)((rest + 127) / 128), 128, 0, s>>>(A, m, k0, kb);
-      dim3 grid((unsigned)((rest + 127) / 128), (unsigned)((rest + 127) / 128));
-      k_gemm_trailing32<<<grid, 256, 0, s>>>(A, m, k0, kb);
+      // A22 -= L21 U12 (rows and columns from k0 + kb on)
+      const int64_t base = k0 + kb;
+      sgemm32(s, rest, rest, kb, -1.f, A + k0 * m + base, m, A + base * m + k0, m, 1.f, A + base * m + base, m);
     }
     STOKES_LAUNCHED();
   }
