@@ -44,6 +44,12 @@ DF64_OPS_PER_PAIR = 129
 # parts 6, rho^2 2, r.a 2, r.sigma 2, coefficient 3, accumulation 2
 F32_OPS_PER_PAIR = 17
 METRIC = "time-to-solution @1e-8 rel. residual; Stokes matvec Gpairs/s vs FLOP peak"
+# DRAM bytes (read + write) per launch of the pair kernels on the 136,192-node
+# workload, from one ncu capture of each shape (profiles/k_dlp_pairs_*_cfg2.md);
+# keyed by (kernel, threads, targets per thread, tile). A shape that is not
+# listed, or a kernel changed since its capture, reports traffic null.
+MEASURED_TRAFFIC = {("k_dlp_pairs_df64", 256, 1, 256): 9820672.0,
+                    ("k_dlp_pairs_f32", 256, 4, 256): 7642624.0}
 
 
 def parse_args():
@@ -508,7 +514,12 @@ def main():
                     "ops_per_pair": ops,
                     "peak_source": "FP32 pipes: 152 SMs x 128 lanes x 2070 MHz, one op per lane per clock",
                     "fp64_class_tflops_at_18_flops_per_pair": round(achieved, 3)}
-    roofline.update({"traffic": None, "gpairs_per_s": round(gps / 1e9, 2), "avg_launch_ms": round(avg_ms, 4),
+    traffic = None
+    if args.workload == "cfg2" and kp in tuned:
+        traffic = MEASURED_TRAFFIC.get((kname, *tuned[kp]["shape"]))
+    roofline.update({"traffic": traffic, "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, "
+                     "one capture of this kernel shape on this workload" if traffic else None,
+                     "gpairs_per_s": round(gps / 1e9, 2), "avg_launch_ms": round(avg_ms, 4),
                      "launches": n_l, "flops_per_pair": FLOPS_PER_PAIR})
     phases = {}
     names = {0: "pairs_fp64", 1: "pairs_fp32", 2: "pairs_df64", 3: "epilogue", 4: "bd_apply", 5: "arnoldi",

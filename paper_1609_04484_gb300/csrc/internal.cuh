@@ -177,6 +177,8 @@ struct TwoGrid {
   DevBuf<double> rc, zc, h;
   DevBuf<float> rc32;
   DevBuf<float> gemv_part;         // column-split partial sums of the coarse apply
+  DevBuf<float2> rpart;            // row-chunk partial sums of the restriction
+  int64_t max_chunks = 0;
   DevBuf<float> work32;
   DevBuf<int> d_pore_ids;
 };

@@ -316,65 +316,111 @@ __global__ void k_trsm_row_panel32(float* __restrict__ A, int64_t m, int64_t k0,
 
 // rc = R r per component (x and y): rc_j = (n_c / n_f) sum_i P[i][j] r_i.
 // Transfers run in single precision (a preconditioner: flexible GMRES
-// absorbs the rounding).
-__global__ void k_restrict(int n_comp, const int64_t* __restrict__ off, const int64_t* __restrict__ off_c,
-                           const int64_t* __restrict__ ioff, const float* __restrict__ P, const double* __restrict__ r,
-                           double* __restrict__ rc, float* __restrict__ rc32, const int* __restrict__ done) {
+// absorbs the rounding). Pass 1: CTA (c, k) takes rows [kRc c, kRc c + kRc)
+// of component k (its r in shared memory) against all n_c columns
+// (coalesced reads of P's rows) and writes partial sums part[c][j]; pass 2
+// adds the chunks of each coarse node in a fixed order.
+constexpr int kRc = 256;
+
+__global__ void __launch_bounds__(128)
+k_restrict_part(const int64_t* __restrict__ off, const int64_t* __restrict__ off_c, const int64_t* __restrict__ ioff,
+                const float* __restrict__ P, const double* __restrict__ r, int64_t Nc, float2* __restrict__ part,
+                const int* __restrict__ done) {
   count_launch();
   if (done && *done) return;
   const int k = blockIdx.y;
   const int64_t nf = off[k + 1] - off[k], nc = off_c[k + 1] - off_c[k];
-  const float* Pk = P + ioff[k];
-  const double2* rk = reinterpret_cast<const double2*>(r) + off[k];
-  const float scale = (float)nc / (float)nf;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nc; j += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t i0 = blockIdx.x * (int64_t)kRc;
+  if (i0 >= nf) return;
+  const int ni = (int)imin64(kRc, nf - i0);
+  __shared__ float2 sr[kRc];
+  const double2* rk = reinterpret_cast<const double2*>(r) + off[k] + i0;
+  for (int e = threadIdx.x; e < ni; e += blockDim.x) {
+    const double2 v = rk[e];
+    sr[e] = make_float2((float)v.x, (float)v.y);
+  }
+  __syncthreads();
+  const float* Pk = P + ioff[k] + i0 * nc;
+  for (int64_t j = threadIdx.x; j < nc; j += blockDim.x) {
     float ax = 0.f, ay = 0.f;
-    for (int64_t i = 0; i < nf; ++i) {
-      const float p = Pk[i * nc + j];
-      const double2 v = rk[i];
-      ax = fmaf(p, (float)v.x, ax);
-      ay = fmaf(p, (float)v.y, ay);
+    for (int i = 0; i < ni; ++i) {
+      const float pv = Pk[i * nc + j];
+      ax = fmaf(pv, sr[i].x, ax);
+      ay = fmaf(pv, sr[i].y, ay);
     }
-    rc[2 * (off_c[k] + j)] = (double)(scale * ax);
-    rc[2 * (off_c[k] + j) + 1] = (double)(scale * ay);
-    rc32[2 * (off_c[k] + j)] = scale * ax;
-    rc32[2 * (off_c[k] + j) + 1] = scale * ay;
+    part[blockIdx.x * Nc + off_c[k] + j] = make_float2(ax, ay);
   }
 }
 
-// z = I zc (+ -2 h on the wall), h = r - I rc
-__global__ void k_prolong(int n_comp, int outer, const int64_t* __restrict__ off, const int64_t* __restrict__ off_c,
-                          const int64_t* __restrict__ ioff, const float* __restrict__ P, const double* __restrict__ r,
-                          const double* __restrict__ rc, const double* __restrict__ zc, double* __restrict__ z,
-                          double* __restrict__ h, const int* __restrict__ done) {
+__global__ void k_restrict_sum(int64_t Nc, const int* __restrict__ comp_c, const int64_t* __restrict__ off,
+                               const int64_t* __restrict__ off_c, const float2* __restrict__ part,
+                               double* __restrict__ rc, float* __restrict__ rc32, const int* __restrict__ done) {
   count_launch();
   if (done && *done) return;
-  const int k = blockIdx.y;
-  const int64_t nf = off[k + 1] - off[k], nc = off_c[k + 1] - off_c[k];
-  const float* Pk = P + ioff[k];
-  const double2* rck = reinterpret_cast<const double2*>(rc) + off_c[k];
-  const double2* zck = reinterpret_cast<const double2*>(zc) + off_c[k];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nf; i += (int64_t)gridDim.x * blockDim.x) {
-    float ux = 0.f, uy = 0.f, vx = 0.f, vy = 0.f;
-    const float* row = Pk + i * nc;
-    for (int64_t j = 0; j < nc; ++j) {
-      const float p = row[j];
-      const double2 zv = zck[j], rv = rck[j];
-      ux = fmaf(p, (float)zv.x, ux);
-      uy = fmaf(p, (float)zv.y, uy);
-      vx = fmaf(p, (float)rv.x, vx);
-      vy = fmaf(p, (float)rv.y, vy);
+  for (int64_t jj = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; jj < Nc; jj += (int64_t)gridDim.x * blockDim.x) {
+    const int k = comp_c[jj];
+    const int64_t nf = off[k + 1] - off[k], nc = off_c[k + 1] - off_c[k];
+    const int64_t chunks = (nf + kRc - 1) / kRc;
+    float ax = 0.f, ay = 0.f;
+    for (int64_t c = 0; c < chunks; ++c) {
+      const float2 v = part[c * Nc + jj];
+      ax += v.x;
+      ay += v.y;
     }
-    const int64_t o = 2 * (off[k] + i);
-    const double hx = r[o] - vx, hy = r[o + 1] - vy;
-    h[o] = hx;
-    h[o + 1] = hy;
-    if (k == outer) {
-      z[o] = ux - 2.0 * hx;
-      z[o + 1] = uy - 2.0 * hy;
-    } else {
-      z[o] = ux;
-      z[o + 1] = uy;
+    const float scale = (float)nc / (float)nf;
+    rc[2 * jj] = (double)(scale * ax);
+    rc[2 * jj + 1] = (double)(scale * ay);
+    rc32[2 * jj] = scale * ax;
+    rc32[2 * jj + 1] = scale * ay;
+  }
+}
+
+// z = I zc (+ -2 h on the wall), h = r - I rc. One warp per fine node: the
+// lanes read the node's row of P (coalesced) and reduce by shuffles.
+__global__ void __launch_bounds__(256)
+k_prolong(int64_t N, int outer, const int* __restrict__ comp, const int64_t* __restrict__ off,
+          const int64_t* __restrict__ off_c, const int64_t* __restrict__ ioff, const float* __restrict__ P,
+          const double* __restrict__ r, const double* __restrict__ rc, const double* __restrict__ zc,
+          double* __restrict__ z, double* __restrict__ h, const int* __restrict__ done) {
+  count_launch();
+  if (done && *done) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t gi = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); gi < N; gi += warps) {
+    const int k = comp[gi];
+    const int64_t i = gi - off[k];
+    const int64_t nc = off_c[k + 1] - off_c[k];
+    const float* row = P + ioff[k] + i * nc;
+    const double2* rck = reinterpret_cast<const double2*>(rc) + off_c[k];
+    const double2* zck = reinterpret_cast<const double2*>(zc) + off_c[k];
+    float ux = 0.f, uy = 0.f, vx = 0.f, vy = 0.f;
+    for (int64_t j = lane; j < nc; j += 32) {
+      const float pv = row[j];
+      const double2 zv = zck[j], rv = rck[j];
+      ux = fmaf(pv, (float)zv.x, ux);
+      uy = fmaf(pv, (float)zv.y, uy);
+      vx = fmaf(pv, (float)rv.x, vx);
+      vy = fmaf(pv, (float)rv.y, vy);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ux += __shfl_xor_sync(0xffffffffu, ux, o);
+      uy += __shfl_xor_sync(0xffffffffu, uy, o);
+      vx += __shfl_xor_sync(0xffffffffu, vx, o);
+      vy += __shfl_xor_sync(0xffffffffu, vy, o);
+    }
+    if (lane == 0) {
+      const int64_t o2 = 2 * gi;
+      const double hx = r[o2] - vx, hy = r[o2 + 1] - vy;
+      h[o2] = hx;
+      h[o2 + 1] = hy;
+      if (k == outer) {
+        z[o2] = ux - 2.0 * hx;
+        z[o2 + 1] = uy - 2.0 * hy;
+      } else {
+        z[o2] = ux;
+        z[o2 + 1] = uy;
+      }
     }
   }
 }
@@ -540,6 +586,10 @@ void twogrid_setup(Geom& g, int q) {
   t.rc32.alloc(m);
   t.zc.alloc(m);
   t.gemv_part.alloc((size_t)kGemvSplits * m);
+  int64_t max_nf = 0;
+  for (int k = 0; k < nc; ++k) max_nf = std::max<int64_t>(max_nf, g.off[k + 1] - g.off[k]);
+  t.max_chunks = (max_nf + kRc - 1) / kRc;
+  t.rpart.alloc((size_t)t.max_chunks * Nc);
   t.h.alloc(2 * g.N);
   // explicit float inverse of the coarse operator: each apply is then one
   // memory-bound matrix-vector product
@@ -559,10 +609,10 @@ static void twogrid_apply(Geom& g, const double* r, double* z, const int* done, 
   TwoGrid& t = g.tg;
   cudaStream_t s = g.stream;
   const int nc = g.n_comp;
-  const int64_t nmax = std::max<int64_t>(1, (g.N + 255) / 256);
-  dim3 gr((unsigned)std::min<int64_t>(16, nmax), (unsigned)nc);
-  k_restrict<<<gr, 128, 0, s>>>(nc, g.d_off.get(), t.d_off_c.get(), t.d_ioff.get(), t.interp.get(), r, t.rc.get(),
-                                t.rc32.get(), done);
+  k_restrict_part<<<dim3((unsigned)t.max_chunks, (unsigned)nc), 128, 0, s>>>(
+      g.d_off.get(), t.d_off_c.get(), t.d_ioff.get(), t.interp.get(), r, t.Nc, t.rpart.get(), done);
+  k_restrict_sum<<<(unsigned)std::min<int64_t>(152 * 4, (t.Nc + 255) / 256), 256, 0, s>>>(
+      t.Nc, t.comp_c.get(), g.d_off.get(), t.d_off_c.get(), t.rpart.get(), t.rc.get(), t.rc32.get(), done);
   STOKES_LAUNCHED();
   const int64_t m = 2 * t.Nc;
   k_dense_gemv32_part<<<dim3((unsigned)((m + 1023) / 1024), kGemvSplits), 256, 0, s>>>(t.inv.get(), m, t.rc32.get(),
@@ -570,9 +620,9 @@ static void twogrid_apply(Geom& g, const double* r, double* z, const int* done, 
   k_dense_gemv32_sum<<<(unsigned)std::min<int64_t>(152 * 4, (m + 255) / 256), 256, 0, s>>>(t.gemv_part.get(), m,
                                                                                          t.zc.get(), done);
   STOKES_LAUNCHED();
-  dim3 gp((unsigned)std::min<int64_t>(64, nmax), (unsigned)nc);
-  k_prolong<<<gp, 128, 0, s>>>(nc, g.outer, g.d_off.get(), t.d_off_c.get(), t.d_ioff.get(), t.interp.get(), r,
-                               t.rc.get(), t.zc.get(), z, t.h.get(), done);
+  k_prolong<<<(unsigned)std::min<int64_t>(152 * 16, (g.N + 7) / 8), 256, 0, s>>>(
+      g.N, g.outer, g.comp.get(), g.d_off.get(), t.d_off_c.get(), t.d_ioff.get(), t.interp.get(), r, t.rc.get(),
+      t.zc.get(), z, t.h.get(), done);
   STOKES_LAUNCHED();
   bd_apply_pores_accumulate(g, t.h.get(), z, done, f32);
 }
