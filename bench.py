@@ -61,7 +61,7 @@ def parse_args():
     p.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg1"])
     p.add_argument("--precision", default=None, choices=["mixed", "df64", "fp64"])
     p.add_argument("--pc", default=None, choices=["bd", "twogrid"])
-    p.add_argument("--coarsen", type=int, default=8)
+    p.add_argument("--coarsen", type=int, default=4)
     p.add_argument("--restart", type=int, default=None)
     p.add_argument("--tol", type=float, default=1e-8)
     p.add_argument("--max-iter", type=int, default=5000)

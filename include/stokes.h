@@ -144,6 +144,18 @@ int stokes_precond_setup(stokes_geom* g, int pc_kind);
  * pivot), STOKES_ECUDA. */
 int stokes_precond_setup_twogrid(stokes_geom* g, int coarsen);
 
+/* The same with a choice of how the coarse operator is applied:
+ *   STOKES_TG_COARSE_AUTO     explicit float inverse up to 40960 coarse
+ *                             unknowns (2 N / coarsen), LU factors above
+ *   STOKES_TG_COARSE_INVERSE  explicit float inverse (2 m^3 more setup
+ *                             flops; each apply one dense GEMV of 4 m^2 bytes)
+ *   STOKES_TG_COARSE_LU       the float LU factors through persistent
+ *                             triangular solves (the same 4 m^2 bytes per
+ *                             apply, no inversion)
+ * stokes_precond_setup_twogrid(g, q) is the AUTO mode. */
+enum stokes_tg_coarse { STOKES_TG_COARSE_AUTO = 0, STOKES_TG_COARSE_INVERSE = 1, STOKES_TG_COARSE_LU = 2 };
+int stokes_precond_setup_twogrid_ex(stokes_geom* g, int coarsen, int coarse_mode);
+
 /* z = P^-1 v with the current preconditioner (for tests and external
  * Krylov codes). v, z [2N]. STOKES_ESTATE if not set up. */
 int stokes_precond_apply(stokes_geom* g, const double* v, double* z);

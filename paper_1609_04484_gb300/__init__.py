@@ -28,6 +28,7 @@ __all__ = [
     "stokes_pair_shape_count", "stokes_pair_shape_info", "stokes_set_pair_shape", "stokes_get_pair_shape",
     "stokes_autotune", "stokes_tune_cache_insert", "stokes_tune_cache_lookup", "stokes_tune_cache_clear",
     "stokes_tune_cache_save", "stokes_tune_cache_load", "stokes_batch_matvec", "stokes_batch_solve",
+    "stokes_precond_setup_twogrid_ex", "STOKES_TG_COARSE_AUTO", "STOKES_TG_COARSE_INVERSE", "STOKES_TG_COARSE_LU",
 ]
 
 STOKES_OK, STOKES_EINVAL, STOKES_ENOMEM, STOKES_ECUDA = 0, -1, -2, -3
@@ -35,6 +36,7 @@ STOKES_ENOTCONV, STOKES_EBREAKDOWN, STOKES_ESTATE = -4, -5, -6
 STOKES_FP64, STOKES_FP32, STOKES_DF64, STOKES_MIXED_IR = 0, 1, 2, 3
 STOKES_PC_NONE, STOKES_PC_BLOCKDIAG, STOKES_PC_TWOGRID = 0, 1, 2
 STOKES_PC_RIGHT, STOKES_PC_LEFT = 0, 1
+STOKES_TG_COARSE_AUTO, STOKES_TG_COARSE_INVERSE, STOKES_TG_COARSE_LU = 0, 1, 2
 (STOKES_PROF_PAIRS_FP64, STOKES_PROF_PAIRS_FP32, STOKES_PROF_PAIRS_DF64, STOKES_PROF_EPILOGUE,
  STOKES_PROF_BD_APPLY, STOKES_PROF_ARNOLDI, STOKES_PROF_BD_SETUP) = range(7)
 
@@ -60,6 +62,7 @@ def _load():
         "stokes_matvec": (I, [P, P, P, I]),
         "stokes_precond_setup": (I, [P, I]),
         "stokes_precond_setup_twogrid": (I, [P, I]),
+        "stokes_precond_setup_twogrid_ex": (I, [P, I, I]),
         "stokes_precond_apply": (I, [P, P, P]),
         "stokes_precond_apply_prec": (I, [P, P, P, I]),
         "stokes_gmres_solve": (I, [P, P, D, I, I, I, I, P, ctypes.POINTER(I), ctypes.POINTER(D),
@@ -156,6 +159,10 @@ def stokes_precond_setup(handle, pc_kind=STOKES_PC_BLOCKDIAG):
 
 def stokes_precond_setup_twogrid(handle, coarsen=8):
     _check(lib.stokes_precond_setup_twogrid(ctypes.c_void_p(handle), int(coarsen)))
+
+
+def stokes_precond_setup_twogrid_ex(handle, coarsen=8, coarse_mode=STOKES_TG_COARSE_AUTO):
+    _check(lib.stokes_precond_setup_twogrid_ex(ctypes.c_void_p(handle), int(coarsen), int(coarse_mode)))
 
 
 def stokes_precond_apply(handle, v, z):

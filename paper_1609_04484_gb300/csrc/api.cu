@@ -138,11 +138,18 @@ int stokes_precond_setup(stokes_geom* h, int pc_kind) {
 }
 
 int stokes_precond_setup_twogrid(stokes_geom* h, int coarsen) {
+  return stokes_precond_setup_twogrid_ex(h, coarsen, STOKES_TG_COARSE_AUTO);
+}
+
+int stokes_precond_setup_twogrid_ex(stokes_geom* h, int coarsen, int coarse_mode) {
   return guarded([&] {
     Geom& g = handle(h);
+    stokes::require(coarse_mode == STOKES_TG_COARSE_AUTO || coarse_mode == STOKES_TG_COARSE_INVERSE ||
+                        coarse_mode == STOKES_TG_COARSE_LU,
+                    "unknown coarse_mode");
     g.tg.ready = false;
     g.bd.ready = false;
-    stokes::twogrid_setup(g, coarsen);
+    stokes::twogrid_setup(g, coarsen, coarse_mode);
   });
 }
 

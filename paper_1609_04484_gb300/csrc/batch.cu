@@ -656,6 +656,9 @@ void batch_init(Batch& b, Geom* const* geoms, int n_geoms, int R) {
   for (Geom* g : b.gs) {
     require(g != nullptr, "null handle");
     require(g->stream == b.s, "all handles of a batch must use the same stream");
+    // the captured cycle holds ordinary kernel launches only
+    require(!(g->tg.ready && g->tg.use_lu),
+            "batched solves need the two-grid coarse solve by its explicit inverse (STOKES_TG_COARSE_INVERSE)");
   }
   b.mom_off.assign(b.S + 1, 0);
   for (int k = 0; k < n_geoms; ++k)

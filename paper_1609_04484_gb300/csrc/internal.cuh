@@ -178,6 +178,7 @@ struct TwoGrid {
   DevBuf<float> rc32;
   DevBuf<float> gemv_part;         // column-split partial sums of the coarse apply
   DevBuf<float2> rpart;            // row-chunk partial sums of the restriction
+  bool use_lu = false;             // coarse solve by the LU factors (else the explicit inverse)
   int64_t max_chunks = 0;
   DevBuf<float> work32;
   DevBuf<int> d_pore_ids;
@@ -293,7 +294,7 @@ void bd_setup(Geom& g);
 void bd_apply(Geom& g, const double* v, double* z, const int* done, bool f32 = false);
 void bd_check_barrier(Geom& g);
 // ---- twogrid.cu ----
-void twogrid_setup(Geom& g, int q);
+void twogrid_setup(Geom& g, int q, int coarse_mode = STOKES_TG_COARSE_AUTO);
 // z = P^-1 v with the current preconditioner (two-grid if set up, else block diagonal)
 void precond_apply(Geom& g, const double* v, double* z, const int* done, bool f32);
 void invert_from_lu32(Geom& g, const float* LU, int64_t m, const int* perm, float* X);

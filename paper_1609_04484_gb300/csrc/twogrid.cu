@@ -30,6 +30,7 @@ void bd_apply_pores_accumulate(Geom& g, const double* h, double* z, const int* d
 namespace {
 
 constexpr int kNb = 64;
+constexpr int64_t kMaxExplicitCoarse = 40960;  // coarse unknowns up to which the inverse is formed
 
 __global__ void k_coarse_gather(int64_t Nc, int q, const int64_t* __restrict__ off, const int64_t* __restrict__ off_c,
                                 int n_comp, const double2* __restrict__ pos, const double2* __restrict__ nrm,
@@ -468,7 +469,7 @@ struct SetupTimer {
   }
 };
 
-void twogrid_setup(Geom& g, int q) {
+void twogrid_setup(Geom& g, int q, int coarse_mode) {
   SetupTimer tm{std::getenv("STOKES_TRACE") != nullptr, g.stream, SetupTimer::now()};
   TwoGrid& t = g.tg;
   t.ready = false;
@@ -548,8 +549,19 @@ void twogrid_setup(Geom& g, int q) {
   pi.alloc(256);
   ivp.alloc(1);
   float* A = t.lu.get();
+  // with STOKES_TRACE: time of the panel factorisations and of the trailing
+  // updates, from events around each phase
+  std::vector<cudaEvent_t> ev;
+  auto mark = [&]() {
+    if (!tm.on) return;
+    cudaEvent_t e;
+    STOKES_CUDA(cudaEventCreate(&e));
+    STOKES_CUDA(cudaEventRecord(e, s));
+    ev.push_back(e);
+  };
   for (int64_t k0 = 0; k0 < m; k0 += kNb) {
     const int kb = (int)std::min<int64_t>(kNb, m - k0);
+    mark();
     for (int64_t c = k0; c < k0 + kb; ++c) {
       const int parts = (int)std::min<int64_t>(256, (m - c + 255) / 256);
       k_piv_partial32<<<parts, 256, 0, s>>>(A, m, c, pv.get(), pi.get());
@@ -562,6 +574,7 @@ void twogrid_setup(Geom& g, int q) {
             A, m, c, k0 + kb, ivp.get());
     }
     const int64_t rest = m - k0 - kb;
+    mark();
     if (rest > 0) {
       k_trsm_row_panel32<<<(unsigned)((rest + 127) / 128), 128, 0, s>>>(A, m, k0, kb);
       // A22 -= L21 U12 (rows and columns from k0 + kb on)
@@ -569,6 +582,19 @@ void twogrid_setup(Geom& g, int q) {
       sgemm32(s, rest, rest, kb, -1.f, A + k0 * m + base, m, A + base * m + k0, m, 1.f, A + base * m + base, m);
     }
     STOKES_LAUNCHED();
+  }
+  mark();
+  if (tm.on) {
+    STOKES_CUDA(cudaStreamSynchronize(s));
+    double panel = 0.0, trail = 0.0;
+    for (size_t e = 0; e + 1 < ev.size(); ++e) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[e], ev[e + 1]);
+      (e % 2 == 0 ? panel : trail) += ms;
+    }
+    for (auto e : ev) cudaEventDestroy(e);
+    std::fprintf(stderr, "[stokes] two-grid LU: panels %.3f s, row panel solves + trailing updates %.3f s\n",
+                 panel / 1e3, trail / 1e3);
   }
   tm.lap("LU");
   std::vector<int> hpiv(m);
@@ -591,12 +617,21 @@ void twogrid_setup(Geom& g, int q) {
   t.max_chunks = (max_nf + kRc - 1) / kRc;
   t.rpart.alloc((size_t)t.max_chunks * Nc);
   t.h.alloc(2 * g.N);
-  // explicit float inverse of the coarse operator: each apply is then one
-  // memory-bound matrix-vector product
-  t.inv.alloc((size_t)m * m);
-  invert_from_lu32(g, t.lu.get(), m, t.perm.get(), t.inv.get());
-  t.lu.release();
-  tm.lap("inverse");
+  // Coarse solve: an explicit float inverse (each apply one memory-bound
+  // matrix-vector product) while forming it is cheap (2 m^3 flops); beyond
+  // kMaxExplicitCoarse unknowns, or on request, the LU factors are applied
+  // by the persistent triangular solves instead (the same bytes per apply,
+  // no inversion).
+  t.use_lu = coarse_mode == STOKES_TG_COARSE_LU || (coarse_mode == STOKES_TG_COARSE_AUTO && m > kMaxExplicitCoarse);
+  if (t.use_lu) {
+    t.inv.release();
+    t.work32.alloc(m);
+  } else {
+    t.inv.alloc((size_t)m * m);
+    invert_from_lu32(g, t.lu.get(), m, t.perm.get(), t.inv.get());
+    t.lu.release();
+    tm.lap("inverse");
+  }
   g.prof.end(ps, s);
   // fine blocks of the pores (the wall block is replaced by -2 I)
   bd_setup_pores(g, /*skip_wall=*/true);
@@ -615,10 +650,14 @@ static void twogrid_apply(Geom& g, const double* r, double* z, const int* done, 
       t.Nc, t.comp_c.get(), g.d_off.get(), t.d_off_c.get(), t.rpart.get(), t.rc.get(), t.rc32.get(), done);
   STOKES_LAUNCHED();
   const int64_t m = 2 * t.Nc;
-  k_dense_gemv32_part<<<dim3((unsigned)((m + 1023) / 1024), kGemvSplits), 256, 0, s>>>(t.inv.get(), m, t.rc32.get(),
-                                                                                     t.gemv_part.get(), done);
-  k_dense_gemv32_sum<<<(unsigned)std::min<int64_t>(152 * 4, (m + 255) / 256), 256, 0, s>>>(t.gemv_part.get(), m,
-                                                                                         t.zc.get(), done);
+  if (t.use_lu) {
+    lu_solve_persistent<float>(g, t.lu.get(), m, t.perm.get(), t.rc.get(), t.zc.get(), t.work32.get(), done);
+  } else {
+    k_dense_gemv32_part<<<dim3((unsigned)((m + 1023) / 1024), kGemvSplits), 256, 0, s>>>(
+        t.inv.get(), m, t.rc32.get(), t.gemv_part.get(), done);
+    k_dense_gemv32_sum<<<(unsigned)std::min<int64_t>(152 * 4, (m + 255) / 256), 256, 0, s>>>(t.gemv_part.get(), m,
+                                                                                           t.zc.get(), done);
+  }
   STOKES_LAUNCHED();
   k_prolong<<<(unsigned)std::min<int64_t>(152 * 16, (g.N + 7) / 8), 256, 0, s>>>(
       g.N, g.outer, g.comp.get(), g.d_off.get(), t.d_off_c.get(), t.d_ioff.get(), t.interp.get(), r, t.rc.get(),

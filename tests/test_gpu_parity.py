@@ -374,17 +374,37 @@ def test_two_grid_solve_matches_dense_oracle(S, dev, prec):
             assert iters <= r_or["iters"] + 3
 
 
-def test_two_grid_apply_matches_oracle(S, dev):
+@pytest.mark.parametrize("mode", ["AUTO", "INVERSE", "LU"])
+def test_two_grid_apply_matches_oracle(S, dev, mode):
     """P^-1 v against the oracle's double-precision two-grid apply: equal up
-    to the float coarse factorisation (coarse condition number x 1e-7)."""
+    to the float coarse factorisation (coarse condition number x 1e-7),
+    with the coarse solve by the explicit inverse or by the LU factors
+    (persistent triangular solves)."""
     g = si.config1_geometry(1, n_outer=256, n_pores=5, n_per_pore=32)
     v = np.random.default_rng(2).standard_normal(2 * g.n_nodes)
     ref = O.TwoGrid(g, 4).apply(v)
     with S.Geometry(g) as G:
-        S.stokes_precond_setup_twogrid(G.handle, 4)
+        S.stokes_precond_setup_twogrid_ex(G.handle, 4, getattr(S, "STOKES_TG_COARSE_" + mode))
         z = np.empty_like(v)
         S.stokes_precond_apply(G.handle, v, z)
         assert rel(z, ref) < 1e-3
+
+
+def test_two_grid_lu_coarse_solve_matches_dense_oracle(S, dev):
+    """The coarse LU applied by triangular solves inside the double-float
+    FGMRES gives the dense FP64 solution."""
+    g = si.config1_geometry(0, n_outer=256, n_pores=6, n_per_pore=32)
+    f = si.pipe_bc(g).reshape(-1)
+    ref = O.solve_dense(g, f)
+    with S.Geometry(g) as G:
+        S.stokes_precond_setup_twogrid_ex(G.handle, 4, S.STOKES_TG_COARSE_LU)
+        sig = np.zeros_like(f)
+        code, iters, rr, _ = S.stokes_gmres_solve(G.handle, f, sig, tol=1e-11, restart=100,
+                                                  precision=S.STOKES_DF64)
+        assert code == S.STOKES_OK and rr <= 1e-11
+        assert rel(sig, ref) < 1e-9
+        with pytest.raises(S.StokesError):
+            S.stokes_precond_setup_twogrid_ex(G.handle, 4, 7)
 
 
 def test_two_grid_rejects_bad_coarsening(S, dev):
