@@ -189,178 +189,6 @@ __global__ void k_copy_rows(const float* __restrict__ src, int64_t lds, float* _
   }
 }
 
-// ---------------------------------------------------------------------------
-// Tensor-core float GEMM with three TF32 products: each operand is split as
-// x = hi + lo with hi = tf32(x), lo = tf32(x - hi), and
-//   A B ~ Ah Bh + Ah Bl + Al Bh
-// (the dropped Al Bl term is ~2^-22 of the product), accumulated in FP32 by
-// mma.sync m16n8k8 TF32 instructions. This keeps about single-precision
-// accuracy, which the float LU of the two-grid coarse operator needs.
-// CTA: 128 x 128 tile of C, 8 warps as 2 (rows) x 4 (columns), each warp
-// 64 x 32 = 4 x 4 MMA tiles. K is staged 16 at a time: hi and lo parts of A
-// ([k][row]) and B ([k][column]) in shared memory, rows padded to 136 floats
-// (136 = 8 mod 32) so that the fragment loads (lanes: row = lane / 4,
-// k = lane % 4) hit 32 distinct banks.
-// ---------------------------------------------------------------------------
-constexpr int kTcK = 16, kTcLd = 136;
-
-__device__ __forceinline__ unsigned tf32_bits(float x) {
-  unsigned r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-__global__ void __launch_bounds__(256)
-k_sgemm_tc(int64_t M, int64_t N, int K, float alpha, const float* __restrict__ A, int64_t lda,
-           const float* __restrict__ B, int64_t ldb, float beta, float* __restrict__ C, int64_t ldc) {
-  count_launch();
-  extern __shared__ __align__(16) float smem[];
-  float* sAh = smem;                      // [kTcK][kTcLd]
-  float* sAl = sAh + kTcK * kTcLd;
-  float* sBh = sAl + kTcK * kTcLd;
-  float* sBl = sBh + kTcK * kTcLd;
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int wm = warp >> 2, wn = warp & 3;        // warp tile: rows 64 wm.., columns 32 wn..
-  const int gid = lane >> 2, tig = lane & 3;
-  const int64_t r0 = blockIdx.x * (int64_t)128, c0 = blockIdx.y * (int64_t)128;
-  float acc[4][4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-  for (int k0 = 0; k0 < K; k0 += kTcK) {
-    __syncthreads();
-    // A tile: 16 k x 128 rows, columns of A are contiguous in rows
-    for (int e = t; e < kTcK * 32; e += 256) {
-      const int kk = e >> 5, rq = (e & 31) * 4;
-      const int64_t r = r0 + rq;
-      const int ka = k0 + kk;
-      float v[4];
-      if (ka < K && r + 3 < M) {
-        const float4 f = *reinterpret_cast<const float4*>(A + (int64_t)ka * lda + r);
-        v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
-      } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = (ka < K && r + q < M) ? A[(int64_t)ka * lda + r + q] : 0.f;
-      }
-      float h[4], l[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        h[q] = __uint_as_float(tf32_bits(v[q]));
-        l[q] = __uint_as_float(tf32_bits(v[q] - h[q]));
-      }
-      *reinterpret_cast<float4*>(sAh + kk * kTcLd + rq) = make_float4(h[0], h[1], h[2], h[3]);
-      *reinterpret_cast<float4*>(sAl + kk * kTcLd + rq) = make_float4(l[0], l[1], l[2], l[3]);
-    }
-    // B tile: 16 k x 128 columns, each column of B holds its k contiguously
-    for (int e = t; e < 128 * (kTcK / 4); e += 256) {
-      const int cc = e >> 2, kq = (e & 3) * 4;
-      const int64_t c = c0 + cc;
-      const int kb = k0 + kq;
-      float v[4];
-      if (c < N && kb + 3 < K) {
-        const float4 f = *reinterpret_cast<const float4*>(B + c * ldb + kb);
-        v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
-      } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = (c < N && kb + q < K) ? B[c * ldb + kb + q] : 0.f;
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float h = __uint_as_float(tf32_bits(v[q]));
-        sBh[(kq + q) * kTcLd + cc] = h;
-        sBl[(kq + q) * kTcLd + cc] = __uint_as_float(tf32_bits(v[q] - h));
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int ks = 0; ks < kTcK; ks += 8) {
-      unsigned ah[4][4], al[4][4], bh[4][2], bl[4][2];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int row = 64 * wm + 16 * i + gid;
-        // A fragment (16 x 8, row-major): (row, k), (row + 8, k), (row, k + 4), (row + 8, k + 4)
-        const int o0 = (ks + tig) * kTcLd + row, o1 = (ks + tig + 4) * kTcLd + row;
-        ah[i][0] = __float_as_uint(sAh[o0]);
-        ah[i][1] = __float_as_uint(sAh[o0 + 8]);
-        ah[i][2] = __float_as_uint(sAh[o1]);
-        ah[i][3] = __float_as_uint(sAh[o1 + 8]);
-        al[i][0] = __float_as_uint(sAl[o0]);
-        al[i][1] = __float_as_uint(sAl[o0 + 8]);
-        al[i][2] = __float_as_uint(sAl[o1]);
-        al[i][3] = __float_as_uint(sAl[o1 + 8]);
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int col = 32 * wn + 8 * j + gid;
-        // B fragment (8 x 8, column-major): (k, col), (k + 4, col)
-        bh[j][0] = __float_as_uint(sBh[(ks + tig) * kTcLd + col]);
-        bh[j][1] = __float_as_uint(sBh[(ks + tig + 4) * kTcLd + col]);
-        bl[j][0] = __float_as_uint(sBl[(ks + tig) * kTcLd + col]);
-        bl[j][1] = __float_as_uint(sBl[(ks + tig + 4) * kTcLd + col]);
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          mma_tf32(acc[i][j], al[i], bh[j]);
-          mma_tf32(acc[i][j], ah[i], bl[j]);
-          mma_tf32(acc[i][j], ah[i], bh[j]);
-        }
-    }
-  }
-  // C fragment (16 x 8): (row, 2 tig), (row, 2 tig + 1), (row + 8, 2 tig), (row + 8, 2 tig + 1)
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int64_t r = r0 + 64 * wm + 16 * i + gid + (e >= 2 ? 8 : 0);
-        const int64_t c = c0 + 32 * wn + 8 * j + 2 * tig + (e & 1);
-        if (r < M && c < N) {
-          float* cp = C + c * ldc + r;
-          const float v = alpha * acc[i][j][e];
-          *cp = beta == 0.f ? v : fmaf(beta, *cp, v);
-        }
-      }
-}
-
-}  // namespace
-
-void sgemm32_tc(cudaStream_t s, int64_t M, int64_t N, int K, float alpha, const float* A, int64_t lda, const float* B,
-                int64_t ldb, float beta, float* C, int64_t ldc) {
-  if (M <= 0 || N <= 0) return;
-  const bool aligned = ((lda | ldb) & 3) == 0 &&
-                       ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) == 0;
-  static const bool simt = std::getenv("STOKES_SGEMM_SIMT") != nullptr;
-  if (!aligned || simt) {
-    sgemm32(s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-    return;
-  }
-  const size_t sm = 4 * (size_t)kTcK * kTcLd * sizeof(float);
-  static bool attr = false;
-  if (!attr) {
-    STOKES_CUDA(cudaFuncSetAttribute(k_sgemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    attr = true;
-  }
-  dim3 grid((unsigned)((M + 127) / 128), (unsigned)((N + 127) / 128));
-  k_sgemm_tc<<<grid, 256, sm, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-  STOKES_LAUNCHED();
-}
-
-namespace {
-
 }  // namespace
 
 void sgemm32(cudaStream_t s, int64_t M, int64_t N, int K, float alpha, const float* A, int64_t lda, const float* B,

@@ -301,11 +301,7 @@ void invert_from_lu32(Geom& g, const float* LU, int64_t m, const int* perm, floa
 // C = alpha A B + beta C, column-major float (M x K times K x N)
 void sgemm32(cudaStream_t s, int64_t M, int64_t N, int K, float alpha, const float* A, int64_t lda, const float* B,
              int64_t ldb, float beta, float* C, int64_t ldc);
-// the same on the tensor cores with three TF32 products (near single
-// precision); falls back to sgemm32 for unaligned operands or when
-// STOKES_SGEMM_SIMT is set
-void sgemm32_tc(cudaStream_t s, int64_t M, int64_t N, int K, float alpha, const float* A, int64_t lda,
-                const float* B, int64_t ldb, float beta, float* C, int64_t ldc);
+
 template <class T>
 void lu_solve_persistent(Geom& g, const T* A, int64_t m, const int* perm, const double* v, double* z, T* work,
                          const int* done);

@@ -579,7 +579,7 @@ void twogrid_setup(Geom& g, int q, int coarse_mode) {
       k_trsm_row_panel32<<<(unsigned)((rest + 127) / 128), 128, 0, s>>>(A, m, k0, kb);
       // A22 -= L21 U12 (rows and columns from k0 + kb on)
       const int64_t base = k0 + kb;
-      sgemm32_tc(s, rest, rest, kb, -1.f, A + k0 * m + base, m, A + base * m + k0, m, 1.f, A + base * m + base, m);
+      sgemm32(s, rest, rest, kb, -1.f, A + k0 * m + base, m, A + base * m + k0, m, 1.f, A + base * m + base, m);
     }
     STOKES_LAUNCHED();
   }
