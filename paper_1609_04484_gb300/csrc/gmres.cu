@@ -288,6 +288,11 @@ static void krylov_alloc(Geom& g, int m) {
   k.scal.alloc(8);
   k.state.alloc(4);
   k.nblk = nblk;
+  if (!k.ring_ready) {
+    STOKES_CUDA(cudaMallocHost(&k.h_done, Krylov::kRing * sizeof(int)));
+    for (auto& e : k.ev) STOKES_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    k.ring_ready = true;
+  }
 }
 
 // ||v|| on the device, copied to the host (synchronises). Needs krylov_alloc.
@@ -421,6 +426,20 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
       k_scale<<<gv, 256, 0, s>>>(k.w.get(), k.scal.get(), 0, vnext, n, state);
       g.prof.end(pa, s);
       STOKES_LAUNCHED();
+      // The host runs at most kAhead iterations ahead of the GPU and stops
+      // enqueueing once the GPU reports convergence: the done flag after
+      // each iteration goes to pinned memory behind an event, and the flag
+      // of iteration j - kAhead is read once that event has completed (the
+      // GPU still has kAhead iterations queued, so it does not idle).
+      constexpr int kAhead = 16;
+      static_assert(Krylov::kRing > kAhead, "ring must outlast the run-ahead");
+      STOKES_CUDA(cudaMemcpyAsync(k.h_done + j % Krylov::kRing, state, sizeof(int), cudaMemcpyDeviceToHost, s));
+      STOKES_CUDA(cudaEventRecord(k.ev[j % Krylov::kRing], s));
+      if (j >= kAhead) {
+        const int jj = j - kAhead;
+        STOKES_CUDA(cudaEventSynchronize(k.ev[jj % Krylov::kRing]));
+        if (k.h_done[jj % Krylov::kRing]) break;
+      }
       if (trace && (j + 1) % 100 == 0) {
         double est = 0.0;
         int st = 0;

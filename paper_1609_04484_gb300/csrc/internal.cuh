@@ -111,6 +111,20 @@ struct Krylov {
   DevBuf<double> V, Z, Zb, w, t, x, f, r, partial, H, cs, sn, g, y, scal;
   DevBuf<int> state;  // [0] done, [1] columns completed, [2] breakdown
   int nblk = 0;
+  // bounded run-ahead of the host: the done flag after each iteration is
+  // copied to pinned memory behind an event (a ring of kRing slots)
+  static constexpr int kRing = 32;
+  int* h_done = nullptr;
+  cudaEvent_t ev[kRing] = {};
+  bool ring_ready = false;
+  Krylov() = default;
+  Krylov(const Krylov&) = delete;
+  Krylov& operator=(const Krylov&) = delete;
+  ~Krylov() {
+    if (h_done) cudaFreeHost(h_done);
+    if (ring_ready)
+      for (auto e : ev) cudaEventDestroy(e);
+  }
 };
 
 // Kernel timing: launches of each kernel class bracketed by CUDA events on
