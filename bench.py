@@ -45,7 +45,7 @@ DF64_OPS_PER_PAIR = 129
 F32_OPS_PER_PAIR = 17
 METRIC = "time-to-solution @1e-8 rel. residual; Stokes matvec Gpairs/s vs FLOP peak"
 # DRAM bytes (read + write) per launch of the pair kernels on the 136,192-node
-# workload, from one ncu capture of each shape (profiles/k_dlp_pairs_*_cfg2.md);
+# workload, from one ncu capture of each shape (profiles/k_dlp_pairs_*_pipe1000.md);
 # keyed by (kernel, threads, targets per thread, tile). A shape that is not
 # listed, or a kernel changed since its capture, reports traffic null.
 MEASURED_TRAFFIC = {("k_dlp_pairs_df64", 256, 1, 256): 9820672.0,
@@ -58,7 +58,7 @@ def parse_args():
     p.add_argument("--steps", type=int, default=1)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg1"])
+    p.add_argument("--workload", default="pipe1000", choices=["pipe1000", "pipe10"])
     p.add_argument("--precision", default=None, choices=["mixed", "df64", "fp64"])
     p.add_argument("--pc", default=None, choices=["bd", "twogrid"])
     p.add_argument("--coarsen", type=int, default=4)
@@ -82,7 +82,7 @@ def parse_args():
 
 
 def workload_config(name):
-    if name == "cfg2":
+    if name == "pipe1000":
         return {"workload": "porous pipe, 1000 pores x 128 nodes + 8192-node wall (N=136192, 272384 unknowns)",
                 "outer": "|x/20|^8+|y/2|^8=1", "pores": 1000, "nodes_per_pore": 128, "wall_nodes": 8192,
                 "bc": "pipe flow", "tol": 1e-8}
@@ -153,7 +153,7 @@ def solver_params(args):
     (block diagonal, GMRES(50), FP64); the 136,192-node case needs the
     two-grid preconditioner and a long Krylov basis to converge in minutes,
     with double-float operators and FP64 true residuals."""
-    big = args.workload == "cfg2"
+    big = args.workload == "pipe1000"
     prec = args.precision or ("df64" if big else "fp64")
     pc = args.pc or ("twogrid" if big else "bd")
     restart = args.restart or (600 if big else 50)
@@ -196,7 +196,7 @@ def run_reference(args):
     # iteration count of the plain block-diagonal solve at this size is
     # taken from the GPU run when known; the reference leg assumes the same
     # number of operator applications (its time is a lower bound)
-    iters = int(os.environ.get("STOKES_REF_ITERS", "500" if args.workload == "cfg2" else "49"))
+    iters = int(os.environ.get("STOKES_REF_ITERS", "23" if args.workload == "pipe1000" else "67"))
     times = []
     info = None
     for s in range(args.warmup + args.steps):
@@ -385,7 +385,7 @@ def main():
     prec = {"mixed": S.STOKES_MIXED_IR, "df64": S.STOKES_DF64, "fp64": S.STOKES_FP64}[prec_name]
     vel_prec = S.STOKES_FP64 if prec_name == "fp64" else S.STOKES_DF64
     max_iter = args.max_iter
-    tol = args.tol if args.workload == "cfg2" else min(args.tol, 1e-10)
+    tol = args.tol if args.workload == "pipe1000" else min(args.tol, 1e-10)
 
     d = lambda a: torch.tensor(np.ascontiguousarray(a).reshape(-1), dtype=torch.float64, device=dev)
     nodes, normals = d(geom.nodes), d(geom.normals)
@@ -515,7 +515,7 @@ def main():
                     "peak_source": "FP32 pipes: 152 SMs x 128 lanes x 2070 MHz, one op per lane per clock",
                     "fp64_class_tflops_at_18_flops_per_pair": round(achieved, 3)}
     traffic = None
-    if args.workload == "cfg2" and kp in tuned:
+    if args.workload == "pipe1000" and kp in tuned:
         traffic = MEASURED_TRAFFIC.get((kname, *tuned[kp]["shape"]))
     roofline.update({"traffic": traffic, "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, "
                      "one capture of this kernel shape on this workload" if traffic else None,

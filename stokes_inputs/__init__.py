@@ -35,7 +35,7 @@ import numpy as np
 __all__ = [
     "cached_geometry",
     "Geometry", "superellipse_curve", "circle_curve", "assemble_geometry",
-    "place_pores", "config1_geometry", "config2_geometry", "batch_geometry",
+    "place_pores", "pipe10_geometry", "pipe1000_geometry", "batch_geometry",
     "pipe_bc", "reversed_pipe_bc", "outer_shear_bc", "shear_bc",
     "translation_bc", "rotation_bc", "stokeslet_rotlet_bc",
     "stokeslet_rotlet_velocity", "interior_targets", "random_density",
@@ -343,20 +343,20 @@ def _build(rng_seed, outer_shape, n_outer, radius_sampler, n_pores, n_per_pore,
     return assemble_geometry(pores, outer, outer_shape, info)
 
 
-def config1_geometry(seed: int = 0, n_outer: int = 512, n_pores: int = 10, n_per_pore: int = 64):
+def pipe10_geometry(seed: int = 0, n_outer: int = 512, n_pores: int = 10, n_per_pore: int = 64):
     """Outer |x/4|^8 + |y|^8 = 1 (512 nodes); 10 pores, radii U[0.1, 0.2],
     centres uniform in |x| < 3.2, |y| < 0.6, gap >= 0.05; 64 nodes per
     pore (N = 1152 nodes, 2304 unknowns)."""
     return _build(seed, (4.0, 1.0, 8), n_outer,
                   lambda rng, m: rng.uniform(0.1, 0.2, m), n_pores, n_per_pore,
-                  0.05, (-3.2, 3.2, -0.6, 0.6), False, {"name": "cfg1"})
+                  0.05, (-3.2, 3.2, -0.6, 0.6), False, {"name": "pipe10"})
 
 
 def _lognormal_radii(rng, m, median=0.15, sigma=0.3, lo=0.05, hi=0.3):
     return np.clip(rng.lognormal(math.log(median), sigma, m), lo, hi)
 
 
-def config2_geometry(seed: int = 0, n_outer: int = 8192, n_pores: int = 1000, n_per_pore: int = 128):
+def pipe1000_geometry(seed: int = 0, n_outer: int = 8192, n_pores: int = 1000, n_per_pore: int = 128):
     """Outer |x/20|^8 + |y/2|^8 = 1 (8192 nodes); 1000 pores with radii
     lognormal (median 0.15, sigma 0.3) clipped to [0.05, 0.3], gap >= 0.05,
     128 nodes per pore (N = 136,192 nodes, 272,384 unknowns).
@@ -365,14 +365,14 @@ def config2_geometry(seed: int = 0, n_outer: int = 8192, n_pores: int = 1000, n_
     random-sequential-adsorption limit, so pores are placed largest first and
     all radii shrink by 0.95 until placement succeeds (scale in info)."""
     return _build(seed, (20.0, 2.0, 8), n_outer, _lognormal_radii, n_pores, n_per_pore,
-                  0.05, None, True, {"name": "cfg2"})
+                  0.05, None, True, {"name": "pipe1000"})
 
 
 def batch_geometry(index: int, n_pores=None, n_per_pore=None, n_outer=None):
     """One geometry of the uneven multi-geometry batch: pore count uniform in
     [50, 800], nodes per pore in {64, 128, 256}, wall nodes in
     {2048, 4096, 8192}; wall |x/a|^8 + |y/2|^8 = 1 with a set so the pores
-    fill ~30 % of the area; radii as in config2_geometry. Seed = index."""
+    fill ~30 % of the area; radii as in pipe1000_geometry. Seed = index."""
     rng = np.random.default_rng(10_000 + index)
     M = int(rng.integers(50, 801)) if n_pores is None else int(n_pores)
     npp = int(rng.choice([64, 128, 256])) if n_per_pore is None else int(n_per_pore)
@@ -542,8 +542,8 @@ def _source_tag() -> str:
 
 
 def cached_geometry(name: str, seed: int = 0, cache_dir=None) -> Geometry:
-    """config1_geometry / config2_geometry / batch_geometry /
-    batch_small_geometry by name ("cfg1", "cfg2", "batch<i>", "batchsmall<i>"), stored as .npz under `cache_dir`
+    """pipe10_geometry / pipe1000_geometry / batch_geometry /
+    batch_small_geometry by name ("pipe10", "pipe1000", "batch<i>", "batchsmall<i>"), stored as .npz under `cache_dir`
     (default: <repo>/.cache) keyed by the generator's source hash."""
     import os
     import pathlib
@@ -557,10 +557,10 @@ def cached_geometry(name: str, seed: int = 0, cache_dir=None) -> Geometry:
         return Geometry(z["nodes"], z["normals"], z["weights"], z["curvature"], z["offsets"],
                         int(z["outer_comp"]), z["centres"], z["radii"],
                         tuple(float(v) for v in z["outer_shape"]), info)
-    if name == "cfg1":
-        g = config1_geometry(seed)
-    elif name == "cfg2":
-        g = config2_geometry(seed)
+    if name == "pipe10":
+        g = pipe10_geometry(seed)
+    elif name == "pipe1000":
+        g = pipe1000_geometry(seed)
     elif name.startswith("batchsmall"):
         g = batch_small_geometry(int(name[10:]))
     elif name.startswith("batch"):

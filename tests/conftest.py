@@ -17,10 +17,10 @@ def pytest_configure(config):
 def small_geom():
     """4 pores x 32 nodes + 256-node wall |x/4|^8 + |y|^8 = 1 (384 nodes)."""
     import stokes_inputs as si
-    return si.config1_geometry(0, n_outer=256, n_pores=4, n_per_pore=32)
+    return si.pipe10_geometry(0, n_outer=256, n_pores=4, n_per_pore=32)
 
 
 @pytest.fixture(scope="session")
-def cfg1_geom():
+def pipe10_geom():
     import stokes_inputs as si
-    return si.cached_geometry("cfg1", 0)
+    return si.cached_geometry("pipe10", 0)

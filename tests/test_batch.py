@@ -23,8 +23,8 @@ def _outer_only():
 
 
 def _geoms():
-    return [_ragged(), si.config1_geometry(1, n_outer=128, n_pores=3, n_per_pore=32), _outer_only(),
-            si.cached_geometry("cfg1", 0)]
+    return [_ragged(), si.pipe10_geometry(1, n_outer=128, n_pores=3, n_per_pore=32), _outer_only(),
+            si.cached_geometry("pipe10", 0)]
 
 
 def _rhs(g, r):
@@ -144,7 +144,7 @@ def test_batch_solve_agrees_with_single_solves(S, gpu):
     within 2, and starts from the given initial guess."""
     torch = gpu
     dev = torch.device("cuda:0")
-    geoms = [si.cached_geometry("cfg1", 0), si.config1_geometry(2, n_outer=256, n_pores=5, n_per_pore=32)]
+    geoms = [si.cached_geometry("pipe10", 0), si.pipe10_geometry(2, n_outer=256, n_pores=5, n_per_pore=32)]
     Gs = [S.Geometry(g) for g in geoms]
     try:
         fs, xs, single = [], [], []
@@ -177,7 +177,7 @@ def test_batch_solve_agrees_with_single_solves(S, gpu):
 @pytest.mark.gpu
 def test_batch_rejects_host_arrays_and_mixed_streams(S, gpu):
     torch = gpu
-    g = si.config1_geometry(0, n_outer=96, n_pores=2, n_per_pore=16)
+    g = si.pipe10_geometry(0, n_outer=96, n_pores=2, n_per_pore=16)
     G = S.Geometry(g)
     st = torch.cuda.Stream()
     G2 = S.Geometry(g, stream=st.cuda_stream)

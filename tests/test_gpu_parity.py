@@ -51,10 +51,10 @@ def _outer_only():
 
 
 GEOMS = {
-    "cfg1": lambda: si.cached_geometry("cfg1", 0),
+    "pipe10": lambda: si.cached_geometry("pipe10", 0),
     "ragged": _ragged_geometry,
     "outer_only": _outer_only,
-    "one_pore": lambda: si.config1_geometry(3, n_outer=96, n_pores=1, n_per_pore=40),
+    "one_pore": lambda: si.pipe10_geometry(3, n_outer=96, n_pores=1, n_per_pore=40),
 }
 
 
@@ -106,7 +106,7 @@ def test_gmres_iteration_count_matches_oracle_gmres(S, dev):
     """Same method (right block-diagonal GMRES(50), tol 1e-10) on the
     1152-node pipe problem: iteration counts within 2 (different rounding:
     CGS2 on the GPU, MGS in the oracle)."""
-    g = si.cached_geometry("cfg1", 0)
+    g = si.cached_geometry("pipe10", 0)
     f = si.pipe_bc(g).reshape(-1)
     r_or = O.solve_gmres(g, f, tol=1e-10, restart=50, precond="bd")
     with S.Geometry(g) as G:
@@ -120,7 +120,7 @@ def test_gmres_iteration_count_matches_oracle_gmres(S, dev):
 
 @pytest.mark.parametrize("side", ["left", "none"])
 def test_gmres_left_and_unpreconditioned(S, dev, side):
-    g = si.config1_geometry(0, n_outer=256, n_pores=4, n_per_pore=32)
+    g = si.pipe10_geometry(0, n_outer=256, n_pores=4, n_per_pore=32)
     f = si.pipe_bc(g).reshape(-1)
     ref = O.solve_dense(g, f)
     with S.Geometry(g) as G:
@@ -136,7 +136,7 @@ def test_gmres_left_and_unpreconditioned(S, dev, side):
 
 
 def test_velocity_matches_oracle(S, dev):
-    g = si.cached_geometry("cfg1", 0)
+    g = si.cached_geometry("pipe10", 0)
     sig = O.solve_dense(g, si.pipe_bc(g).reshape(-1))
     T = si.interior_targets(g, 4096, min_dist=0.05, seed=11)
     ref = O.velocity(g, sig, T)
@@ -148,7 +148,7 @@ def test_velocity_matches_oracle(S, dev):
 
 def test_exact_stokeslet_flow_through_gpu_solve(S, dev):
     """End to end against the closed form of Eq. 13 (not just the oracle)."""
-    g = si.config1_geometry(2, n_outer=512, n_pores=4, n_per_pore=64)
+    g = si.pipe10_geometry(2, n_outer=512, n_pores=4, n_per_pore=64)
     c, lam, mu = si.stokeslet_rotlet_params(g, 0)
     f = si.stokeslet_rotlet_velocity(g.nodes, c, lam, mu).reshape(-1)
     T = si.interior_targets(g, 300, min_dist=0.3, seed=5)
@@ -163,7 +163,7 @@ def test_exact_stokeslet_flow_through_gpu_solve(S, dev):
 
 
 def test_errors_are_reported(S, dev):
-    g = si.config1_geometry(0, n_outer=64, n_pores=2, n_per_pore=16)
+    g = si.pipe10_geometry(0, n_outer=64, n_pores=2, n_per_pore=16)
     bad = g.offsets.copy()
     bad[1] = bad[0] + 4                 # a component with fewer than 8 nodes
     with pytest.raises(S.StokesError) as e:
@@ -195,7 +195,7 @@ def test_errors_are_reported(S, dev):
 def test_full_size_matvec_sampled_rows(S, dev, rows):
     """136,192-node geometry (1000 pores), launch shape as in the benchmark:
     sampled rows of A sigma against the oracle's matrix-free rows."""
-    g = si.cached_geometry("cfg2", 0)
+    g = si.cached_geometry("pipe1000", 0)
     sig = si.random_density(g, 9).reshape(-1)
     idx = np.random.default_rng(1).choice(g.n_nodes, rows, replace=False)
     idx = np.concatenate([idx, [0, g.n_nodes - 1, int(g.offsets[g.outer_comp])]])
@@ -239,7 +239,7 @@ def test_block_diagonal_float_inverses(S, dev):
 def test_full_size_block_diagonal_sampled_rows(S, dev):
     """136,192-node geometry: for sampled rows i of each sampled block k,
     (A_kk z_k)_i equals v_i, with A_kk's rows from the oracle."""
-    g = si.cached_geometry("cfg2", 0)
+    g = si.cached_geometry("pipe1000", 0)
     v = np.random.default_rng(7).standard_normal(2 * g.n_nodes)
     with S.Geometry(g) as G:
         S.stokes_precond_setup(G.handle, S.STOKES_PC_BLOCKDIAG)
@@ -271,7 +271,7 @@ def test_matvec_reduced_precision_matches_oracle(S, dev, case, prec, bound):
 
 @pytest.mark.parametrize("prec,bound", [("DF64", 1e-12), ("FP32", 2e-6)])
 def test_velocity_reduced_precision(S, dev, prec, bound):
-    g = si.cached_geometry("cfg1", 0)
+    g = si.cached_geometry("pipe10", 0)
     sig = si.random_density(g, 5).reshape(-1)
     T = si.interior_targets(g, 1000, min_dist=0.05, seed=12)
     ref = O.velocity(g, sig, T)
@@ -287,7 +287,7 @@ def test_gmres_reduced_precision_solves_to_fp64_accuracy(S, dev, prec):
     relative residual of 1e-11 (the double-float operator's own accuracy is
     ~1e-12 relative, so refinement stalls near there) and the dense FP64
     solution."""
-    g = si.cached_geometry("cfg1", 0)
+    g = si.cached_geometry("pipe10", 0)
     f = si.pipe_bc(g).reshape(-1)
     ref = O.solve_dense(g, f)
     with S.Geometry(g) as G:
@@ -302,7 +302,7 @@ def test_gmres_reduced_precision_solves_to_fp64_accuracy(S, dev, prec):
 
 
 def test_profile_records_pair_launches(S, dev):
-    g = si.cached_geometry("cfg1", 0)
+    g = si.cached_geometry("pipe10", 0)
     f = si.pipe_bc(g).reshape(-1)
     with S.Geometry(g) as G:
         S.stokes_precond_setup(G.handle)
@@ -343,7 +343,7 @@ def test_mixed_refinement_with_triangular_wall_block(S, dev):
 def test_unrestarted_gmres_long_basis(S, dev):
     """A Krylov basis longer than 1000 vectors (no restart) on the
     1152-node problem without preconditioner."""
-    g = si.cached_geometry("cfg1", 0)
+    g = si.cached_geometry("pipe10", 0)
     f = si.pipe_bc(g).reshape(-1)
     ref = O.solve_dense(g, f)
     with S.Geometry(g) as G:
@@ -358,7 +358,7 @@ def test_two_grid_solve_matches_dense_oracle(S, dev, prec):
     """Flexible GMRES with the two-grid preconditioner reaches the dense FP64
     solution, in about as many iterations as the oracle's two-grid FGMRES
     (whose coarse LU is double: the float one here may cost a few more)."""
-    g = si.config1_geometry(0, n_outer=256, n_pores=6, n_per_pore=32)
+    g = si.pipe10_geometry(0, n_outer=256, n_pores=6, n_per_pore=32)
     f = si.pipe_bc(g).reshape(-1)
     A = O.assemble(g)
     ref = np.linalg.solve(A, f)
@@ -380,7 +380,7 @@ def test_two_grid_apply_matches_oracle(S, dev, mode):
     to the float coarse factorisation (coarse condition number x 1e-7),
     with the coarse solve by the explicit inverse or by the LU factors
     (persistent triangular solves)."""
-    g = si.config1_geometry(1, n_outer=256, n_pores=5, n_per_pore=32)
+    g = si.pipe10_geometry(1, n_outer=256, n_pores=5, n_per_pore=32)
     v = np.random.default_rng(2).standard_normal(2 * g.n_nodes)
     ref = O.TwoGrid(g, 4).apply(v)
     with S.Geometry(g) as G:
@@ -393,7 +393,7 @@ def test_two_grid_apply_matches_oracle(S, dev, mode):
 def test_two_grid_lu_coarse_solve_matches_dense_oracle(S, dev):
     """The coarse LU applied by triangular solves inside the double-float
     FGMRES gives the dense FP64 solution."""
-    g = si.config1_geometry(0, n_outer=256, n_pores=6, n_per_pore=32)
+    g = si.pipe10_geometry(0, n_outer=256, n_pores=6, n_per_pore=32)
     f = si.pipe_bc(g).reshape(-1)
     ref = O.solve_dense(g, f)
     with S.Geometry(g) as G:
@@ -408,7 +408,7 @@ def test_two_grid_lu_coarse_solve_matches_dense_oracle(S, dev):
 
 
 def test_two_grid_rejects_bad_coarsening(S, dev):
-    g = si.config1_geometry(0, n_outer=96, n_pores=2, n_per_pore=24)
+    g = si.pipe10_geometry(0, n_outer=96, n_pores=2, n_per_pore=24)
     with S.Geometry(g) as G:
         with pytest.raises(S.StokesError) as e:
             S.stokes_precond_setup_twogrid(G.handle, 5)    # 24 not a multiple of 5
@@ -424,7 +424,7 @@ def test_full_size_two_grid_solve_reaches_tolerance(S, dev):
     nodes from the oracle's matrix-free rows agrees with the GPU residual
     there; the velocity at sampled interior points equals the oracle's
     velocity of the GPU density."""
-    g = si.cached_geometry("cfg2", 0)
+    g = si.cached_geometry("pipe1000", 0)
     f = si.pipe_bc(g).reshape(-1)
     with S.Geometry(g) as G:
         S.stokes_precond_setup_twogrid(G.handle, 4)

@@ -49,8 +49,8 @@ def test_circle_pore_conventions():
     assert abs(c.weights.sum() - 2 * math.pi * 0.15) < 1e-15
 
 
-def test_config1_shape_and_gaps(cfg1_geom):
-    g = cfg1_geom
+def test_config1_shape_and_gaps(pipe10_geom):
+    g = pipe10_geom
     assert g.n_nodes == 1152 and g.n_pores == 10 and g.outer_comp == 10
     assert list(np.diff(g.offsets)) == [64] * 10 + [512]
     pc, pr = g.centres[:10], g.radii[:10]
@@ -63,22 +63,22 @@ def test_config1_shape_and_gaps(cfg1_geom):
     assert (np.linalg.norm(pc[:, None] - wall[None], axis=2) - pr[:, None]).min() >= 0.05 - 1e-3
 
 
-def test_pipe_data_compatible(cfg1_geom):
-    f = si.pipe_bc(cfg1_geom)
-    flux = (cfg1_geom.weights[:, None] * f * cfg1_geom.normals).sum()
+def test_pipe_data_compatible(pipe10_geom):
+    f = si.pipe_bc(pipe10_geom)
+    flux = (pipe10_geom.weights[:, None] * f * pipe10_geom.normals).sum()
     assert abs(flux) < 1e-13
-    assert np.all(f[: cfg1_geom.offsets[-2]] == 0)
+    assert np.all(f[: pipe10_geom.offsets[-2]] == 0)
 
 
-def test_targets_clear_of_boundary(cfg1_geom):
-    T = si.interior_targets(cfg1_geom, 500, min_dist=0.05, seed=3)
+def test_targets_clear_of_boundary(pipe10_geom):
+    T = si.interior_targets(pipe10_geom, 500, min_dist=0.05, seed=3)
     assert T.shape == (500, 2)
-    d = np.linalg.norm(T[:, None] - cfg1_geom.nodes[None], axis=2).min(1)
+    d = np.linalg.norm(T[:, None] - pipe10_geom.nodes[None], axis=2).min(1)
     assert d.min() >= 0.05 - 1e-9
     assert (si.superellipse_inside(T, 4.0, 1.0) < 1).all()
 
 
 def test_generator_deterministic():
-    a = si.config1_geometry(5, n_outer=128, n_pores=3, n_per_pore=16)
-    b = si.config1_geometry(5, n_outer=128, n_pores=3, n_per_pore=16)
+    a = si.pipe10_geometry(5, n_outer=128, n_pores=3, n_per_pore=16)
+    b = si.pipe10_geometry(5, n_outer=128, n_pores=3, n_per_pore=16)
     assert np.array_equal(a.nodes, b.nodes)

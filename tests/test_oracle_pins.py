@@ -97,14 +97,14 @@ def test_smallest_singular_value_stable_under_refinement():
     the mesh is refined."""
     smins = []
     for npp, no in ((16, 128), (32, 256), (64, 512)):
-        g = si.config1_geometry(1, n_outer=no, n_pores=3, n_per_pore=npp)
+        g = si.pipe10_geometry(1, n_outer=no, n_pores=3, n_per_pore=npp)
         smins.append(np.linalg.svd(O.assemble(g), compute_uv=False)[-1])
     assert smins[-1] > 0.5 * smins[0]
 
 
 @pytest.fixture(scope="module")
 def fine_geom():
-    return si.config1_geometry(2, n_outer=512, n_pores=4, n_per_pore=64)
+    return si.pipe10_geometry(2, n_outer=512, n_pores=4, n_per_pore=64)
 
 
 @pytest.mark.parametrize("case", ["translation", "rotation", "shear"])
@@ -134,7 +134,7 @@ def test_stokeslet_rotlet_exact_and_spectral_convergence():
     geometrically under refinement (trapezoid rule on analytic curves)."""
     errs = []
     for npp, no in ((16, 128), (32, 256), (64, 512)):
-        g = si.config1_geometry(2, n_outer=no, n_pores=4, n_per_pore=npp)
+        g = si.pipe10_geometry(2, n_outer=no, n_pores=4, n_per_pore=npp)
         c, lam, mu = si.stokeslet_rotlet_params(g, 0)
         s = O.solve_dense(g, si.stokeslet_rotlet_velocity(g.nodes, c, lam, mu))
         T = si.interior_targets(g, 200, min_dist=0.3, seed=5)
@@ -200,20 +200,20 @@ def test_block_diagonal_is_exact_inverse_of_blocks(small_geom):
         assert np.array_equal(bd.blocks[k], A[a:b, a:b])
 
 
-def test_bd_gmres_fewer_iterations_than_none(cfg1_geom):
+def test_bd_gmres_fewer_iterations_than_none(pipe10_geom):
     """Sec. 4.1: block-diagonal preconditioning cuts the iteration count."""
-    f = si.pipe_bc(cfg1_geom)
-    r_bd = O.solve_gmres(cfg1_geom, f, tol=1e-8, restart=50, precond="bd")
-    r_no = O.solve_gmres(cfg1_geom, f, tol=1e-8, restart=50, precond=None)
+    f = si.pipe_bc(pipe10_geom)
+    r_bd = O.solve_gmres(pipe10_geom, f, tol=1e-8, restart=50, precond="bd")
+    r_no = O.solve_gmres(pipe10_geom, f, tol=1e-8, restart=50, precond=None)
     assert r_bd["relres"] <= 1e-8 and r_no["relres"] <= 1e-8
     assert r_bd["iters"] < 0.5 * r_no["iters"]
 
 
-def test_pipe_flow_no_net_flux_around_a_pore(cfg1_geom):
+def test_pipe_flow_no_net_flux_around_a_pore(pipe10_geom):
     """Incompressibility and no slip (Eq. 1-2): the flux of u through any
     closed curve in the fluid that encloses one pore is zero; the flux
     through a vertical cut equals the flux leaving the wall beyond it."""
-    g = cfg1_geom
+    g = pipe10_geom
     f = si.pipe_bc(g)
     s = O.solve_gmres(g, f, tol=1e-12, restart=50)["x"]
     pc, pr = g.centres[: g.n_pores], g.radii[: g.n_pores]
@@ -262,7 +262,7 @@ def test_coarse_geometry_is_the_trapezoid_rule_on_every_qth_node(small_geom):
 
 
 def test_two_grid_fgmres_solves_the_dense_system_faster_than_block_diagonal():
-    g = si.config1_geometry(0, n_outer=256, n_pores=6, n_per_pore=32)
+    g = si.pipe10_geometry(0, n_outer=256, n_pores=6, n_per_pore=32)
     f = si.pipe_bc(g).reshape(-1)
     A = O.assemble(g)
     ref = np.linalg.solve(A, f)

@@ -141,7 +141,7 @@ def test_every_shape_matches_oracle(S, prec, bound):
 def test_autotune_picks_a_shape_and_caches_it(S, tmp_path):
     _gpu_S(S)
     import stokes_inputs as si
-    g = si.cached_geometry("cfg1", 0)
+    g = si.cached_geometry("pipe10", 0)
     S.stokes_tune_cache_clear()
     sig = si.random_density(g, 1).reshape(-1)
     with S.Geometry(g) as G:

@@ -24,12 +24,12 @@ def _dev(a):
     return torch.tensor(np.ascontiguousarray(a).reshape(-1), dtype=torch.float64, device="cuda:0")
 
 
-@pytest.mark.parametrize("which", ["cfg1", "ragged"])
+@pytest.mark.parametrize("which", ["pipe10", "ragged"])
 def test_noalloc_matvec_matches_the_handle_matvec_on_two_calls(which):
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
     import paper_1609_04484_gb300 as S
-    g = si.cached_geometry("cfg1", 0) if which == "cfg1" else _ragged()
+    g = si.cached_geometry("pipe10", 0) if which == "pipe10" else _ragged()
     arrs = [_dev(a) for a in (g.nodes, g.normals, g.weights, g.curvature)]
     centres = np.ascontiguousarray(g.centres).reshape(-1)
     stream = torch.cuda.current_stream().cuda_stream
@@ -50,7 +50,7 @@ def test_noalloc_rejects_host_arrays_and_oversize_problems():
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
     import paper_1609_04484_gb300 as S
-    g = si.cached_geometry("cfg1", 0)
+    g = si.cached_geometry("pipe10", 0)
     centres = np.ascontiguousarray(g.centres).reshape(-1)
     host = [np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
             for a in (g.nodes, g.normals, g.weights, g.curvature)]
