@@ -9,12 +9,12 @@
 // lower diagonal block in shared memory; a grid barrier ends the phase.
 // The backward sweep mirrors it from the last tile with U's diagonal.
 //
-// The grid barrier spins on a generation counter with an iteration limit:
-// on timeout it raises an error flag, every CTA leaves at the next check,
-// and the host reports the failure instead of hanging.
+// The grid barrier (grid_sync.cuh) spins with an iteration limit: on
+// timeout it raises an error flag, every CTA leaves at the next check, and
+// the host reports the failure instead of hanging.
 #include <algorithm>
 
-#include "internal.cuh"
+#include "grid_sync.cuh"
 
 namespace stokes {
 
@@ -22,41 +22,8 @@ namespace {
 
 constexpr int kTs = 64;
 constexpr int kThreads = 256;
-constexpr long long kSpinLimit = 1ll << 22;  // x ~256 ns sleep: about one second
-
-struct Barrier {
-  unsigned* count;
-  unsigned* gen;
-  int* err;
-};
-
-// Returns false if the barrier timed out (here or in another CTA).
-__device__ bool grid_sync(const Barrier& b) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned* vgen = b.gen;
-    const unsigned g0 = *vgen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(b.count, 1u) + 1u;
-    if (arrived == gridDim.x) {
-      *b.count = 0u;
-      __threadfence();
-      atomicAdd(b.gen, 1u);
-    } else {
-      long long spins = 0;
-      while (*vgen == g0) {
-        if (++spins > kSpinLimit || *(volatile int*)b.err) {
-          atomicExch(b.err, 1);
-          break;
-        }
-        __nanosleep(256);
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return *(volatile int*)b.err == 0;
-}
+using gsync::Barrier;
+using gsync::grid_sync;
 
 template <class T>
 __global__ void __launch_bounds__(kThreads)

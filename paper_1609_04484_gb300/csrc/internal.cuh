@@ -193,6 +193,7 @@ struct TwoGrid {
   DevBuf<float> gemv_part;         // column-split partial sums of the coarse apply
   DevBuf<float2> rpart;            // row-chunk partial sums of the restriction
   bool use_lu = false;             // coarse solve by the LU factors (else the explicit inverse)
+  DevBuf<unsigned> barrier;        // grid barrier of the cooperative panel factorisation
   int64_t max_chunks = 0;
   DevBuf<float> work32;
   DevBuf<int> d_pore_ids;

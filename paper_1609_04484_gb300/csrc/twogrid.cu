@@ -19,8 +19,9 @@
 #include <cstdlib>
 #include <ctime>
 #include <map>
+#include <string>
 
-#include "internal.cuh"
+#include "grid_sync.cuh"
 
 namespace stokes {
 
@@ -294,6 +295,72 @@ __global__ void k_panel_update32(float* __restrict__ A, int64_t m, int64_t c, in
   }
 }
 
+// One panel [k0, k0 + kb) of the blocked LU in a single cooperative launch
+// (every CTA resident), the same steps as k_piv_partial32, k_piv_swap32 and
+// k_panel_update32 per column with grid barriers between them:
+//   1. each CTA's largest |A[r][c]|, r >= c (ties: smallest row);
+//   2. every CTA reduces the partials in the same order, records the pivot,
+//      swaps rows c and p over all m columns (its share of the columns);
+//   3. rows r > c: l = A[r][c] / pivot, A[r][q] -= l A[c][q] for the panel's
+//      later columns q.
+// part holds gridDim.x (value, signed value, row) partials.
+__global__ void __launch_bounds__(256)
+k_panel_lu32(float* __restrict__ A, int64_t m, int64_t k0, int kb, float* __restrict__ pv,
+             int64_t* __restrict__ pi, int* __restrict__ piv, int* __restrict__ status, gsync::Barrier bar) {
+  count_launch();
+  const int G = gridDim.x;
+  const int64_t stride = (int64_t)G * blockDim.x;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  __shared__ int64_t s_p;
+  __shared__ float s_inv;
+  for (int64_t c = k0; c < k0 + kb; ++c) {
+    float best = -1.f;
+    int64_t bi = INT64_MAX;
+    for (int64_t r = c + tid; r < m; r += stride) {
+      const float v = fabsf(A[c * m + r]);
+      if (v > best) { best = v; bi = r; }
+    }
+    argmax_reduce_f(best, bi);
+    if (threadIdx.x == 0) {
+      pv[blockIdx.x] = best;
+      pv[G + blockIdx.x] = bi < m ? A[c * m + bi] : 0.f;
+      pi[blockIdx.x] = bi;
+    }
+    if (!gsync::grid_sync(bar)) return;
+    if (threadIdx.x == 0) {
+      float b = -1.f, d = 0.f;
+      int64_t p = INT64_MAX;
+      for (int q = 0; q < G; ++q)
+        if (pv[q] > b || (pv[q] == b && pi[q] < p)) { b = pv[q]; p = pi[q]; d = pv[G + q]; }
+      if (p >= m) { p = c; d = 0.f; }
+      s_p = p;
+      const bool bad = d == 0.f || !isfinite(d);
+      s_inv = bad ? 0.f : 1.f / d;
+      if (blockIdx.x == 0) {
+        piv[c] = (int)p;
+        if (bad) atomicExch(status, 1);
+      }
+    }
+    __syncthreads();
+    const int64_t p = s_p;
+    const float iv = s_inv;
+    if (p != c)
+      for (int64_t q = tid; q < m; q += stride) {
+        const float t = A[q * m + c];
+        A[q * m + c] = A[q * m + p];
+        A[q * m + p] = t;
+      }
+    if (!gsync::grid_sync(bar)) return;
+    const int64_t pend = k0 + kb;
+    for (int64_t r = c + 1 + tid; r < m; r += stride) {
+      const float l = A[c * m + r] * iv;
+      A[c * m + r] = l;
+      for (int64_t q = c + 1; q < pend; ++q) A[q * m + r] -= l * A[q * m + c];
+    }
+    if (!gsync::grid_sync(bar)) return;
+  }
+}
+
 __global__ void k_trsm_row_panel32(float* __restrict__ A, int64_t m, int64_t k0, int kb) {
   count_launch();
   const int64_t q = k0 + kb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -545,9 +612,25 @@ void twogrid_setup(Geom& g, int q, int coarse_mode) {
   STOKES_CUDA(cudaMemsetAsync(t.status.get(), 0, sizeof(int), s));
   DevBuf<float> pv, ivp;
   DevBuf<int64_t> pi;
-  pv.alloc(512);
-  pi.alloc(256);
+  // Large coarse operators factor each panel in one cooperative launch
+  // (one CTA per SM); small ones (few rows per CTA) keep the per-column
+  // launches. STOKES_TG_PANEL=coop or =launches overrides the choice.
+  const char* panel_env = std::getenv("STOKES_TG_PANEL");
+  const bool force_coop = panel_env && std::string(panel_env) == "coop";
+  const bool force_launches = panel_env && std::string(panel_env) == "launches";
+  int coop_grid = 0;
+  if ((m >= 8192 || force_coop) && !force_launches) {
+    int dev = 0, nsm = 0, per_sm = 0;
+    STOKES_CUDA(cudaGetDevice(&dev));
+    STOKES_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    STOKES_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_panel_lu32, 256, 0));
+    if (per_sm >= 1) coop_grid = nsm;
+  }
+  pv.alloc(std::max(512, 2 * coop_grid));
+  pi.alloc(std::max(256, coop_grid));
   ivp.alloc(1);
+  t.barrier.alloc(4);
+  STOKES_CUDA(cudaMemsetAsync(t.barrier.get(), 0, 4 * sizeof(unsigned), s));
   float* A = t.lu.get();
   // with STOKES_TRACE: time of the panel factorisations and of the trailing
   // updates, from events around each phase
@@ -562,16 +645,28 @@ void twogrid_setup(Geom& g, int q, int coarse_mode) {
   for (int64_t k0 = 0; k0 < m; k0 += kNb) {
     const int kb = (int)std::min<int64_t>(kNb, m - k0);
     mark();
-    for (int64_t c = k0; c < k0 + kb; ++c) {
-      const int parts = (int)std::min<int64_t>(256, (m - c + 255) / 256);
-      k_piv_partial32<<<parts, 256, 0, s>>>(A, m, c, pv.get(), pi.get());
-      k_piv_swap32<<<(unsigned)std::min<int64_t>(64, (m + 255) / 256), 256, 0, s>>>(A, m, c, parts, pv.get(), pi.get(),
-                                                                                   t.piv.get(), t.status.get(),
-                                                                                   ivp.get());
-      const int64_t nr = m - c - 1;
-      if (nr > 0)
-        k_panel_update32<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(1024, (nr + 127) / 128)), 128, 0, s>>>(
-            A, m, c, k0 + kb, ivp.get());
+    if (coop_grid > 0) {
+      gsync::Barrier bar{t.barrier.get(), t.barrier.get() + 1, (int*)(t.barrier.get() + 2)};
+      int64_t k0v = k0;
+      int kbv = kb;
+      float* pvp = pv.get();
+      int64_t* pip = pi.get();
+      int* pivp = t.piv.get();
+      int* stp = t.status.get();
+      void* args[] = {(void*)&A, (void*)&m, (void*)&k0v, (void*)&kbv, (void*)&pvp, (void*)&pip, (void*)&pivp,
+                      (void*)&stp, (void*)&bar};
+      STOKES_CUDA(cudaLaunchCooperativeKernel((const void*)k_panel_lu32, dim3(coop_grid), dim3(256), args, 0, s));
+    } else {
+      for (int64_t c = k0; c < k0 + kb; ++c) {
+        const int parts = (int)std::min<int64_t>(256, (m - c + 255) / 256);
+        k_piv_partial32<<<parts, 256, 0, s>>>(A, m, c, pv.get(), pi.get());
+        k_piv_swap32<<<(unsigned)std::min<int64_t>(64, (m + 255) / 256), 256, 0, s>>>(
+            A, m, c, parts, pv.get(), pi.get(), t.piv.get(), t.status.get(), ivp.get());
+        const int64_t nr = m - c - 1;
+        if (nr > 0)
+          k_panel_update32<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(1024, (nr + 127) / 128)), 128, 0,
+                             s>>>(A, m, c, k0 + kb, ivp.get());
+      }
     }
     const int64_t rest = m - k0 - kb;
     mark();
@@ -599,9 +694,12 @@ void twogrid_setup(Geom& g, int q, int coarse_mode) {
   tm.lap("LU");
   std::vector<int> hpiv(m);
   int hstatus = 0;
+  unsigned hbar = 0;
   STOKES_CUDA(cudaMemcpyAsync(hpiv.data(), t.piv.get(), 4 * m, cudaMemcpyDeviceToHost, s));
   STOKES_CUDA(cudaMemcpyAsync(&hstatus, t.status.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+  STOKES_CUDA(cudaMemcpyAsync(&hbar, t.barrier.get() + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   STOKES_CUDA(cudaStreamSynchronize(s));
+  require(hbar == 0, "two-grid: panel factorisation grid barrier timed out", STOKES_ECUDA);
   require(hstatus == 0, "two-grid: singular coarse operator (zero pivot)", STOKES_EBREAKDOWN);
   std::vector<int> perm(m);
   for (int64_t r = 0; r < m; ++r) perm[r] = (int)r;

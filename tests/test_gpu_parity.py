@@ -390,6 +390,29 @@ def test_two_grid_apply_matches_oracle(S, dev, mode):
         assert rel(z, ref) < 1e-3
 
 
+@pytest.mark.parametrize("panel", ["coop", "launches"])
+def test_two_grid_panel_factorisation_paths(S, dev, panel, monkeypatch):
+    """The coarse LU's panels factored by one cooperative launch per panel
+    (grid barriers between the pivot search, the row swap and the update)
+    or by three launches per column: both give the oracle's two-grid apply
+    and the dense solution."""
+    monkeypatch.setenv("STOKES_TG_PANEL", panel)
+    g = si.pipe10_geometry(1, n_outer=256, n_pores=5, n_per_pore=32)
+    v = np.random.default_rng(2).standard_normal(2 * g.n_nodes)
+    ref = O.TwoGrid(g, 4).apply(v)
+    f = si.pipe_bc(g).reshape(-1)
+    sref = O.solve_dense(g, f)
+    with S.Geometry(g) as G:
+        S.stokes_precond_setup_twogrid_ex(G.handle, 4, S.STOKES_TG_COARSE_LU)
+        z = np.empty_like(v)
+        S.stokes_precond_apply(G.handle, v, z)
+        assert rel(z, ref) < 1e-3
+        sig = np.zeros_like(f)
+        code, iters, rr, _ = S.stokes_gmres_solve(G.handle, f, sig, tol=1e-11, restart=100,
+                                                  precision=S.STOKES_DF64)
+        assert code == S.STOKES_OK and rel(sig, sref) < 1e-9
+
+
 def test_two_grid_lu_coarse_solve_matches_dense_oracle(S, dev):
     """The coarse LU applied by triangular solves inside the double-float
     FGMRES gives the dense FP64 solution."""
