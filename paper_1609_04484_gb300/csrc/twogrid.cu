@@ -303,7 +303,19 @@ __global__ void k_panel_update32(float* __restrict__ A, int64_t m, int64_t c, in
 //      swaps rows c and p over all m columns (its share of the columns);
 //   3. rows r > c: l = A[r][c] / pivot, A[r][q] -= l A[c][q] for the panel's
 //      later columns q.
-// part holds gridDim.x (value, signed value, row) partials.
+// A thread's step 3 produces the new column c + 1 on its own rows, so it
+// takes step 1 of column c + 1 there at once: two barriers per column.
+// pv holds gridDim.x absolute and gridDim.x signed partial values, pi their rows.
+__device__ __forceinline__ void panel_partials(float best, int64_t bi, const float* __restrict__ A, int64_t m,
+                                               int64_t c, float* __restrict__ pv, int64_t* __restrict__ pi) {
+  argmax_reduce_f(best, bi);
+  if (threadIdx.x == 0) {
+    pv[blockIdx.x] = best;
+    pv[gridDim.x + blockIdx.x] = bi < m ? A[c * m + bi] : 0.f;
+    pi[blockIdx.x] = bi;
+  }
+}
+
 __global__ void __launch_bounds__(256)
 k_panel_lu32(float* __restrict__ A, int64_t m, int64_t k0, int kb, float* __restrict__ pv,
              int64_t* __restrict__ pi, int* __restrict__ piv, int* __restrict__ status, gsync::Barrier bar) {
@@ -311,22 +323,20 @@ k_panel_lu32(float* __restrict__ A, int64_t m, int64_t k0, int kb, float* __rest
   const int G = gridDim.x;
   const int64_t stride = (int64_t)G * blockDim.x;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t pend = k0 + kb;
   __shared__ int64_t s_p;
   __shared__ float s_inv;
-  for (int64_t c = k0; c < k0 + kb; ++c) {
+  {
     float best = -1.f;
     int64_t bi = INT64_MAX;
-    for (int64_t r = c + tid; r < m; r += stride) {
-      const float v = fabsf(A[c * m + r]);
+    for (int64_t r = k0 + tid; r < m; r += stride) {
+      const float v = fabsf(A[k0 * m + r]);
       if (v > best) { best = v; bi = r; }
     }
-    argmax_reduce_f(best, bi);
-    if (threadIdx.x == 0) {
-      pv[blockIdx.x] = best;
-      pv[G + blockIdx.x] = bi < m ? A[c * m + bi] : 0.f;
-      pi[blockIdx.x] = bi;
-    }
-    if (!gsync::grid_sync(bar)) return;
+    panel_partials(best, bi, A, m, k0, pv, pi);
+  }
+  for (int64_t c = k0; c < pend; ++c) {
+    if (!gsync::grid_sync(bar)) return;  // partials of column c complete
     if (threadIdx.x == 0) {
       float b = -1.f, d = 0.f;
       int64_t p = INT64_MAX;
@@ -350,14 +360,20 @@ k_panel_lu32(float* __restrict__ A, int64_t m, int64_t k0, int kb, float* __rest
         A[q * m + c] = A[q * m + p];
         A[q * m + p] = t;
       }
-    if (!gsync::grid_sync(bar)) return;
-    const int64_t pend = k0 + kb;
+    if (!gsync::grid_sync(bar)) return;  // row swap complete
+    const bool next = c + 1 < pend;
+    float best = -1.f;
+    int64_t bi = INT64_MAX;
     for (int64_t r = c + 1 + tid; r < m; r += stride) {
       const float l = A[c * m + r] * iv;
       A[c * m + r] = l;
       for (int64_t q = c + 1; q < pend; ++q) A[q * m + r] -= l * A[q * m + c];
+      if (next) {
+        const float v = fabsf(A[(c + 1) * m + r]);
+        if (v > best) { best = v; bi = r; }
+      }
     }
-    if (!gsync::grid_sync(bar)) return;
+    if (next) panel_partials(best, bi, A, m, c + 1, pv, pi);
   }
 }
 
