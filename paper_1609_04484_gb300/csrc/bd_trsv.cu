@@ -37,10 +37,11 @@ k_lu_solve_persistent(const T* __restrict__ A, int64_t m, const int* __restrict_
   __shared__ T red[4][kTs];
   const int64_t nt = (m + kTs - 1) / kTs;
   const int G = gridDim.x;
+  unsigned epoch = 0;
   // z = P v
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m; r += (int64_t)G * blockDim.x)
     z[r] = (T)v[perm[r]];
-  if (!grid_sync(bar)) return;
+  if (!grid_sync(bar, epoch)) return;
 
   // Solve the diagonal tile u in place (lower: unit; upper: divide by the diagonal).
   auto solve_tile = [&](int64_t u, bool lower) {
@@ -89,7 +90,7 @@ k_lu_solve_persistent(const T* __restrict__ A, int64_t m, const int* __restrict_
 
   // forward sweep (unit lower L)
   if (blockIdx.x == 0) solve_tile(0, true);
-  if (!grid_sync(bar)) return;
+  if (!grid_sync(bar, epoch)) return;
   for (int64_t t = 0; t + 1 < nt; ++t) {
     const int64_t first = t + 1;
     // this CTA's tiles u > t: u = first + ((blockIdx.x - first) mod G) + k G
@@ -98,11 +99,11 @@ k_lu_solve_persistent(const T* __restrict__ A, int64_t m, const int* __restrict_
       update_tile(u, t);
       if (u == first) solve_tile(u, true);
     }
-    if (!grid_sync(bar)) return;
+    if (!grid_sync(bar, epoch)) return;
   }
   // backward sweep (upper U)
   if ((nt - 1) % G == blockIdx.x) solve_tile(nt - 1, false);
-  if (!grid_sync(bar)) return;
+  if (!grid_sync(bar, epoch)) return;
   for (int64_t t = nt - 1; t > 0; --t) {
     const int64_t first = t - 1;
     // this CTA's tiles u < t, the one nearest the diagonal first
@@ -111,7 +112,7 @@ k_lu_solve_persistent(const T* __restrict__ A, int64_t m, const int* __restrict_
       update_tile(u, t);
       if (u == first) solve_tile(u, false);
     }
-    if (!grid_sync(bar)) return;
+    if (!grid_sync(bar, epoch)) return;
   }
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m; r += (int64_t)G * blockDim.x)
     out[r] = (double)z[r];

@@ -324,6 +324,7 @@ k_panel_lu32(float* __restrict__ A, int64_t m, int64_t k0, int kb, float* __rest
   const int64_t stride = (int64_t)G * blockDim.x;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t pend = k0 + kb;
+  unsigned epoch = 0;
   __shared__ int64_t s_p;
   __shared__ float s_inv;
   {
@@ -336,19 +337,31 @@ k_panel_lu32(float* __restrict__ A, int64_t m, int64_t k0, int kb, float* __rest
     panel_partials(best, bi, A, m, k0, pv, pi);
   }
   for (int64_t c = k0; c < pend; ++c) {
-    if (!gsync::grid_sync(bar)) return;  // partials of column c complete
-    if (threadIdx.x == 0) {
+    if (!gsync::grid_sync(bar, epoch)) return;  // partials of column c complete
+    if (threadIdx.x < 32) {
+      // warp 0 reduces the G partials: largest value, ties to the smallest
+      // row (the order of the per-column kernels' reduction)
+      const int lane = threadIdx.x;
       float b = -1.f, d = 0.f;
       int64_t p = INT64_MAX;
-      for (int q = 0; q < G; ++q)
+      for (int q = lane; q < G; q += 32)
         if (pv[q] > b || (pv[q] == b && pi[q] < p)) { b = pv[q]; p = pi[q]; d = pv[G + q]; }
-      if (p >= m) { p = c; d = 0.f; }
-      s_p = p;
-      const bool bad = d == 0.f || !isfinite(d);
-      s_inv = bad ? 0.f : 1.f / d;
-      if (blockIdx.x == 0) {
-        piv[c] = (int)p;
-        if (bad) atomicExch(status, 1);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_down_sync(0xffffffffu, b, o);
+        const int64_t op = __shfl_down_sync(0xffffffffu, p, o);
+        const float od = __shfl_down_sync(0xffffffffu, d, o);
+        if (ob > b || (ob == b && op < p)) { b = ob; p = op; d = od; }
+      }
+      if (lane == 0) {
+        if (p >= m) { p = c; d = 0.f; }
+        s_p = p;
+        const bool bad = d == 0.f || !isfinite(d);
+        s_inv = bad ? 0.f : 1.f / d;
+        if (blockIdx.x == 0) {
+          piv[c] = (int)p;
+          if (bad) atomicExch(status, 1);
+        }
       }
     }
     __syncthreads();
@@ -360,7 +373,7 @@ k_panel_lu32(float* __restrict__ A, int64_t m, int64_t k0, int kb, float* __rest
         A[q * m + c] = A[q * m + p];
         A[q * m + p] = t;
       }
-    if (!gsync::grid_sync(bar)) return;  // row swap complete
+    if (!gsync::grid_sync(bar, epoch)) return;  // row swap complete
     const bool next = c + 1 < pend;
     float best = -1.f;
     int64_t bi = INT64_MAX;
@@ -671,6 +684,7 @@ void twogrid_setup(Geom& g, int q, int coarse_mode) {
       int* stp = t.status.get();
       void* args[] = {(void*)&A, (void*)&m, (void*)&k0v, (void*)&kbv, (void*)&pvp, (void*)&pip, (void*)&pivp,
                       (void*)&stp, (void*)&bar};
+      STOKES_CUDA(cudaMemsetAsync(t.barrier.get(), 0, sizeof(unsigned), s));  // arrivals restart; errors stay
       STOKES_CUDA(cudaLaunchCooperativeKernel((const void*)k_panel_lu32, dim3(coop_grid), dim3(256), args, 0, s));
     } else {
       for (int64_t c = k0; c < k0 + kb; ++c) {
