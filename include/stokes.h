@@ -354,6 +354,9 @@ int stokes_batch_matvec(stokes_geom* const* geoms, int n_geoms, int n_rhs, const
  *   iters, relres, status: HOST arrays of n_geoms n_rhs entries (may be
  *   NULL): iterations, true relative residual and STOKES_OK,
  *   STOKES_ENOTCONV or STOKES_EBREAKDOWN of each system.
+ * A geometry whose two-grid coarse solve runs on its LU factors
+ * (STOKES_TG_COARSE_LU, or AUTO above 40960 coarse unknowns) is rejected
+ * with STOKES_EINVAL: the captured cycle holds ordinary launches only.
  * The call returns STOKES_OK when it ran (per-system outcomes are in
  * status), else STOKES_EINVAL, STOKES_ENOMEM or STOKES_ECUDA. */
 int stokes_batch_solve(stokes_geom* const* geoms, int n_geoms, int n_rhs, const double* const* f, double tol,
