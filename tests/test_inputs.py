@@ -49,7 +49,7 @@ def test_circle_pore_conventions():
     assert abs(c.weights.sum() - 2 * math.pi * 0.15) < 1e-15
 
 
-def test_config1_shape_and_gaps(pipe10_geom):
+def test_pipe10_shape_and_gaps(pipe10_geom):
     g = pipe10_geom
     assert g.n_nodes == 1152 and g.n_pores == 10 and g.outer_comp == 10
     assert list(np.diff(g.offsets)) == [64] * 10 + [512]
@@ -82,3 +82,25 @@ def test_generator_deterministic():
     a = si.pipe10_geometry(5, n_outer=128, n_pores=3, n_per_pore=16)
     b = si.pipe10_geometry(5, n_outer=128, n_pores=3, n_per_pore=16)
     assert np.array_equal(a.nodes, b.nodes)
+
+
+@pytest.mark.parametrize("index", [0, 7])
+def test_scaled_down_batch_geometry(index):
+    """The uneven batch's geometries: pore counts in [20, 120], 64 or 128
+    nodes per pore, 1024 or 2048 wall nodes, gaps >= 0.05 between pores and
+    to the wall, pipe data compatible, node counts divisible by 8 (the
+    two-grid coarsening of the batch benchmark)."""
+    g = si.batch_small_geometry(index)
+    M = g.n_pores
+    assert 20 <= M <= 120 and g.outer_comp == M
+    sizes = np.diff(g.offsets)
+    assert len(set(sizes[:M])) == 1 and sizes[0] in (64, 128) and sizes[M] in (1024, 2048)
+    assert all(n % 8 == 0 for n in sizes)
+    pc, pr = g.centres[:M], g.radii[:M]
+    d = np.linalg.norm(pc[:, None] - pc[None], axis=2) - pr[:, None] - pr[None]
+    np.fill_diagonal(d, np.inf)
+    assert d.min() >= 0.05
+    wall = g.nodes[g.comp_slice(M)]
+    assert (np.linalg.norm(pc[:, None] - wall[None], axis=2) - pr[:, None]).min() >= 0.05 - 2e-3
+    f = si.pipe_bc(g)
+    assert abs((g.weights[:, None] * f * g.normals).sum()) < 1e-12
