@@ -248,6 +248,19 @@ def test_trig_interpolation_is_exact_for_band_limited_data():
         assert np.abs(P[:: nf // nc] - np.eye(nc)).max() < 1e-13 if nf % nc == 0 else True
 
 
+def test_restriction_is_the_left_inverse_of_interpolation_up_to_nyquist():
+    """R = (n_c / n_f) I^T undoes the interpolation I on every Fourier mode
+    of the coarse grid except the Nyquist mode: by discrete orthogonality of
+    the modes on the fine grid, (n_c / n_f) I^T I = Id - v v^T / (2 n_c) with
+    v_j = (-1)^j, the Nyquist cosine split evenly between +-n_c / 2 keeping
+    half its weight. A wrong restriction scale or Nyquist split fails it."""
+    for nc, nf in ((8, 32), (16, 64), (8, 64), (32, 128), (128, 1024)):
+        P = O.trig_interpolation(nc, nf)
+        M = (nc / nf) * P.T @ P
+        v = (-1.0) ** np.arange(nc)
+        assert np.abs(M - (np.eye(nc) - np.outer(v, v) / (2 * nc))).max() < 1e-13
+
+
 def test_coarse_geometry_is_the_trapezoid_rule_on_every_qth_node(small_geom):
     g = small_geom
     gc = O.coarse_geometry(g, 4)
