@@ -94,7 +94,7 @@ def test_batch_matvec_matches_oracle(S, gpu, prec, bound, R):
         for s_idx, (y, ref, y1) in enumerate(zip(ys, refs, single)):
             assert _rel(y.cpu().numpy(), ref) < bound, s_idx
             # same arithmetic as the single-geometry kernel up to the partial-sum order
-            assert _rel(y.cpu().numpy(), y1.cpu().numpy()) < (1e-6 if prec == "FP32" else 1e-13), s_idx
+            assert _rel(y.cpu().numpy(), y1.cpu().numpy()) < bound / 10, s_idx
     finally:
         for G in Gs:
             G.close()
@@ -125,11 +125,11 @@ def test_batch_solve_matches_dense_oracle(S, gpu, prec):
                 refs.append(O.solve_dense(g, f))
                 fs.append(torch.tensor(f, device=dev))
                 xs.append(torch.zeros_like(fs[-1]))
-        iters, relres, status = S.stokes_batch_solve([G.handle for G in Gs], R, fs, xs, tol=1e-10, restart=40,
+        iters, relres, status = S.stokes_batch_solve([G.handle for G in Gs], R, fs, xs, tol=1e-11, restart=40,
                                                      max_iter=3000, precision=getattr(S, "STOKES_" + prec))
         for s_idx in range(len(fs)):
             assert status[s_idx] == S.STOKES_OK, (s_idx, status, relres)
-            assert relres[s_idx] <= 1e-10, (s_idx, relres[s_idx])
+            assert relres[s_idx] <= 1e-11, (s_idx, relres[s_idx])
             assert _rel(xs[s_idx].cpu().numpy(), refs[s_idx]) < 1e-8, s_idx
             assert iters[s_idx] > 0
     finally:

@@ -298,3 +298,124 @@ def test_fgmres_tolerates_a_varying_preconditioner(small_geom):
     r = O.fgmres(lambda v: A @ v, f, noisy, tol=1e-11, restart=100)
     assert r["relres"] <= 1e-11
     assert np.linalg.norm(r["x"] - np.linalg.solve(A, f)) < 1e-9 * np.linalg.norm(r["x"])
+
+
+# ---------------------------------------------------------------------------
+# Exact pins of the two-grid apply P^-1 r = I Ac^-1 R r + B^-1 (r - I R r)
+# (wall remainder scaled by -2): three special cases in which the result
+# has a closed form built only from pieces pinned above (the interpolation,
+# the coarse trapezoid rule, the dense operator and its blocks).
+# ---------------------------------------------------------------------------
+
+def _high_band_residual(g, q, seed):
+    """A residual with, on every component, only the fine-grid Fourier modes
+    m with n_c / 2 < m <= n_f / 2 (n_c = n_f / q) in both vector components:
+    by discrete orthogonality the restriction maps it to zero."""
+    rng = np.random.default_rng(seed)
+    r = np.zeros((g.n_nodes, 2))
+    for k in range(g.n_comp):
+        sl = g.comp_slice(k)
+        nf = sl.stop - sl.start
+        nc = nf // q
+        t = 2 * np.pi * np.arange(nf) / nf
+        for m in range(nc // 2 + 1, nf // 2 + 1):
+            for comp in range(2):
+                a, b = rng.standard_normal(2)
+                r[sl, comp] += a * np.cos(m * t) + (b * np.sin(m * t) if 2 * m != nf else 0.0)
+    return r.reshape(-1)
+
+
+def _nyquist_free_coarse_vector(gc, seed):
+    """Random coarse vector orthogonal, per component and per vector
+    component, to that component's alternating vector (-1)^j."""
+    rng = np.random.default_rng(seed)
+    c = rng.standard_normal((gc.n_nodes, 2))
+    for k in range(gc.n_comp):
+        sl = gc.comp_slice(k)
+        v = (-1.0) ** np.arange(sl.stop - sl.start)
+        c[sl] -= np.outer(v, v @ c[sl]) / (v @ v)
+    return c.reshape(-1)
+
+
+def _two_grid_pin_errors(tg_cls, q=4, seed=0):
+    """Relative errors of the three closed-form cases for a TwoGrid class.
+    (1) q = 1: I = R = Id, so the apply is A^-1 r.
+    (2) R r = 0: the coarse part vanishes and the remainder is r itself, so
+        the apply is B^-1 r on the pores and -2 r on the wall.
+    (3) r = I c with c free of the Nyquist vectors: R I c = c, so the
+        remainder vanishes and the apply is I Ac^-1 c."""
+    import scipy.linalg as sla
+    g = si.pipe10_geometry(0, n_outer=256, n_pores=4, n_per_pore=32)
+    A = O.assemble(g)
+    rng = np.random.default_rng(seed)
+    errs = {}
+    # (1)
+    r = rng.standard_normal(2 * g.n_nodes)
+    z = tg_cls(g, 1).apply(r)
+    ref = np.linalg.solve(A, r)
+    errs["q1"] = np.linalg.norm(z - ref) / np.linalg.norm(ref)
+    tg = tg_cls(g, q)
+    # (2)
+    r = _high_band_residual(g, q, seed)
+    assert np.linalg.norm(tg.R @ r) < 1e-12 * np.linalg.norm(r)
+    z = tg.apply(r)
+    ref = np.empty_like(r)
+    for k in range(g.n_comp):
+        a, b = 2 * int(g.offsets[k]), 2 * int(g.offsets[k + 1])
+        if k == g.outer_comp:
+            ref[a:b] = -2.0 * r[a:b]
+        else:
+            ref[a:b] = np.linalg.solve(A[a:b, a:b], r[a:b])
+    errs["kernel_of_R"] = np.linalg.norm(z - ref) / np.linalg.norm(ref)
+    # (3)
+    gc = O.coarse_geometry(g, q)
+    c = _nyquist_free_coarse_vector(gc, seed + 1)
+    Ic = sla.block_diag(*[O.trig_interpolation((g.offsets[k + 1] - g.offsets[k]) // q,
+                                               g.offsets[k + 1] - g.offsets[k]) for k in range(g.n_comp)])
+    Ic = np.kron(Ic, np.eye(2))
+    z = tg.apply(Ic @ c)
+    ref = Ic @ np.linalg.solve(O.assemble(gc), c)
+    errs["range_of_I"] = np.linalg.norm(z - ref) / np.linalg.norm(ref)
+    return errs
+
+
+def test_two_grid_apply_closed_forms():
+    errs = _two_grid_pin_errors(O.TwoGrid)
+    assert max(errs.values()) < 1e-12, errs
+
+
+class _WrongWallScale(O.TwoGrid):
+    """Planted mistake: the wall remainder scaled by -1 instead of -2."""
+
+    def apply(self, r):
+        z = super().apply(r)
+        h = np.asarray(r, dtype=np.float64).reshape(-1) - self.I @ (self.R @ r)
+        z[self.wall] += h[self.wall]
+        return z
+
+
+class _WrongRestrictionScale(O.TwoGrid):
+    """Planted mistake: R = I^T without the n_c / n_f factor."""
+
+    def __init__(self, geom, q):
+        super().__init__(geom, q)
+        if q > 1:
+            self.R = self.R * q
+
+
+class _RemainderNotSplit(O.TwoGrid):
+    """Planted mistake: the pore blocks act on r instead of r - I R r."""
+
+    def apply(self, r):
+        import scipy.linalg as sla
+        r = np.asarray(r, dtype=np.float64).reshape(-1)
+        zc = sla.lu_solve(self.lu, self.R @ r)
+        zh = self.bd.apply(r)
+        zh[self.wall] = -2.0 * r[self.wall]
+        return self.I @ zc + zh
+
+
+@pytest.mark.parametrize("cls", [_WrongWallScale, _WrongRestrictionScale, _RemainderNotSplit])
+def test_two_grid_closed_forms_catch_planted_mistakes(cls):
+    errs = _two_grid_pin_errors(cls)
+    assert max(errs.values()) > 1e-3, errs
