@@ -44,10 +44,10 @@ DF64_OPS_PER_PAIR = 129
 # parts 6, rho^2 2, r.a 2, r.sigma 2, coefficient 3, accumulation 2
 F32_OPS_PER_PAIR = 17
 METRIC = "time-to-solution @1e-8 rel. residual; Stokes matvec Gpairs/s vs FLOP peak"
-# DRAM bytes (read + write) per launch of the pair kernels on the 136,192-node
-# workload, from one ncu capture of each shape (profiles/k_dlp_pairs_*_pipe1000.md);
-# keyed by (kernel, threads, targets per thread, tile). A shape that is not
-# listed, or a kernel changed since its capture, reports traffic null.
+# DRAM bytes (read + write) per launch of a kernel on the 136,192-node
+# workload, from one ncu capture of that kernel shape (the summaries are kept
+# with the profiles); keyed by (kernel, threads, targets per thread, tile). A
+# kernel or shape not listed, or changed since its capture, reports null.
 MEASURED_TRAFFIC = {("k_dlp_pairs_df64", 256, 1, 256): 9820672.0,
                     ("k_dlp_pairs_f32", 256, 4, 256): 7642624.0}
 
@@ -68,6 +68,10 @@ def parse_args():
     p.add_argument("--targets", type=int, default=4096)
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-sub-records", dest="sub_records", action="store_false",
+                   help="skip the other configurations' records (measured once after the timed region)")
+    p.add_argument("--baseline-budget", type=float, default=150.0,
+                   help="seconds for the plain FP64 block-diagonal GMRES baseline (0: skip)")
     p.add_argument("--no-tune", action="store_true", help="skip the pair kernels' launch-shape autotuner")
     p.add_argument("--kernel-bench", action="store_true",
                    help="time only operator applications (A sigma) of each precision on the workload")
@@ -161,58 +165,131 @@ def solver_params(args):
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle leg: bounded sample of the same workload
+# CPU oracle legs (the only code here that runs the oracle)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(geom, iters, budget_s=15.0):
-    """Times the oracle's matrix-free operator rows (FP64 numpy) on a sample
-    of rows and extrapolates to the pair work of a solve of `iters`
-    iterations (one operator application per iteration + one per restart is
-    ignored: a lower bound on the oracle's time)."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _rows_worker(args):
+    """One worker of the all-core oracle sample: random rows of A sigma for
+    `budget_s` seconds; returns (rows, seconds)."""
+    name, seed, budget_s = args
     import oracle
     import stokes_inputs as si
+    geom = si.cached_geometry(name, 0)
     sig = si.random_density(geom, 2).reshape(-1)
-    rng = np.random.default_rng(0)
-    rows_done = 0
+    rng = np.random.default_rng(seed)
+    rows = 0
     t0 = time.perf_counter()
     while time.perf_counter() - t0 < budget_s:
-        rows = rng.choice(geom.n_nodes, 256, replace=False)
-        oracle.apply_rows(geom, sig, rows)
-        rows_done += rows.size
-    el = time.perf_counter() - t0
-    pairs = rows_done * geom.n_nodes
-    pairs_per_s = pairs / el
-    full_matvec_s = geom.n_nodes ** 2 / pairs_per_s
-    return {"pairs_per_s": pairs_per_s, "sample_rows": rows_done, "sample_s": el,
-            "est_time_to_solution_s": iters * full_matvec_s, "cores": 1}
+        rr = rng.choice(geom.n_nodes, 64, replace=False)
+        oracle.apply_rows(geom, sig, rr)
+        rows += rr.size
+    return rows, time.perf_counter() - t0
+
+
+def cpu_baseline_operator_rate(name, budget_s):
+    """The oracle's matrix-free operator rows (numpy FP64) on every host
+    core (a process pool started with spawn, one single-threaded numpy per
+    worker) for `budget_s` seconds: returns the oracle's pair rate and the
+    time of one full operator application A sigma it implies."""
+    import multiprocessing as mp
+    import stokes_inputs as si
+    n_nodes = si.cached_geometry(name, 0).n_nodes  # generated once, before the workers read the cache
+    cores = host_cores()
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            t0 = time.perf_counter()
+            res = pool.map(_rows_worker, [(name, 1000 + c, budget_s) for c in range(cores)])
+            wall = time.perf_counter() - t0
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    rows = sum(r for r, _ in res)
+    busy = max(t for _, t in res)
+    pairs_per_s = rows * n_nodes / busy
+    return {"pairs_per_s": pairs_per_s, "rows": rows, "cores": cores, "busy_s": busy, "wall_s": wall,
+            "matvec_s": n_nodes ** 2 / pairs_per_s}
+
+
+def cpu_baseline_small_solve(geom, f, tol, restart):
+    """The oracle's own plain method solved for real on a small geometry:
+    dense assembly, block-diagonal LU, right-preconditioned GMRES(restart)
+    to `tol`; also its dense LU solution (the FP64 reference the GPU results
+    are compared with)."""
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.solve_gmres(geom, f, tol=tol, restart=restart, max_iter=5000, precond="bd")
+    t_solve = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    x_dense = oracle.solve_dense(geom, f)
+    t_dense = time.perf_counter() - t0
+    return {"gmres_s": t_solve, "iters": r["iters"], "relres": r["relres"], "x": r["x"],
+            "dense_lu_s": t_dense, "x_dense": x_dense}
+
+
+def cpu_baseline_velocity(geom, sigma, targets):
+    import oracle
+    return oracle.velocity(geom, sigma, targets)
 
 
 def run_reference(args):
+    """The oracle timed on the host cores (rank 0 only). The 1152-node
+    workload is solved for real each step; for the 136,192-node workload a
+    step is a bounded all-core sample of the oracle's operator rows, scaled
+    to the operator applications of the two-grid flexible GMRES solve (the
+    same method as the GPU arm; the oracle's coarse setup is not counted, so
+    the value is an estimate and a lower bound)."""
     world, rank, local, pg = dist_setup(args)
     if rank != 0:
         return
     import stokes_inputs as si
     geom = si.cached_geometry(args.workload, 0)
-    # iteration count of the plain block-diagonal solve at this size is
-    # taken from the GPU run when known; the reference leg assumes the same
-    # number of operator applications (its time is a lower bound)
-    iters = int(os.environ.get("STOKES_REF_ITERS", "23" if args.workload == "pipe1000" else "67"))
+    f = si.pipe_bc(geom).reshape(-1)
+    cfg = workload_config(args.workload)
     times = []
     info = None
+    per_step = max(2.0, min(15.0, 150.0 / max(1, args.warmup + args.steps)))
+    applications = int(os.environ.get("STOKES_REF_APPLICATIONS", "25"))
     for s in range(args.warmup + args.steps):
-        info = oracle_sample(geom, iters, budget_s=8.0)
+        if args.workload == "pipe10":
+            r = cpu_baseline_small_solve(geom, f, tol=1e-10, restart=50)
+            t = r["gmres_s"]
+            info = {"cores": 1, "sample": f"full oracle solve: dense assembly, block-diagonal LU, GMRES(50) to "
+                                          f"1e-10 ({r['iters']} iterations, numpy FP64, one core)",
+                    "estimate": False}
+        else:
+            o = cpu_baseline_operator_rate(args.workload, per_step)
+            t = applications * o["matvec_s"]
+            info = {"cores": o["cores"],
+                    "sample": f"{o['rows']} random rows of A sigma on {o['cores']} cores in {o['busy_s']:.1f} s "
+                              f"(numpy FP64, {o['pairs_per_s'] / 1e6:.1f} Mpairs/s): one operator application "
+                              f"{o['matvec_s']:.1f} s, times the {applications} applications of the two-grid "
+                              f"flexible GMRES solve",
+                    "estimate": True}
         if s >= args.warmup:
-            times.append(info["est_time_to_solution_s"])
+            times.append(t)
     v = float(np.mean(times))
-    cfg = workload_config(args.workload)
     line = {"metric": METRIC, "value": v, "unit": "s", "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": v, "unit": "s", "cores": info["cores"], "kind": "oracle",
-                             "sample": f"{info['sample_rows']} random rows of A sigma per step (numpy FP64, "
-                                       f"{info['pairs_per_s']/1e6:.1f} Mpairs/s), extrapolated to {iters} "
-                                       f"full operator applications"},
+                             "sample": info["sample"], "estimate": info["estimate"]},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if info["estimate"]:
+        line["estimate_note"] = ("value is the oracle's time scaled from a bounded sample, not a timed solve: "
+                                 "each step ran for about %.0f s" % per_step)
     print(json.dumps(line), flush=True)
 
 
@@ -419,7 +496,7 @@ def main():
                                                        max_iter=args.max_iter, precision=prec)
             S.stokes_eval_velocity(h, arrs[5], arrs[6], arrs[7], vel_prec)
             if profile:
-                for kind in range(7):
+                for kind in range(10):
                     n, ms, units = S.stokes_profile_read(h, kind)
                     a = prof_acc.setdefault(kind, [0, 0.0, 0.0])
                     a[0] += n
@@ -490,48 +567,33 @@ def main():
 
     if rank != 0:
         return
-    # roofline of the dominant pair kernel
-    pair_kinds = {S.STOKES_PROF_PAIRS_FP64: ("k_dlp_pairs_f64", "fp64"),
-                  S.STOKES_PROF_PAIRS_FP32: ("k_dlp_pairs_f32", "fp32"),
-                  S.STOKES_PROF_PAIRS_DF64: ("k_dlp_pairs_df64", "df64")}
-    dom = max(pair_kinds, key=lambda k: prof_acc.get(k, [0, 0.0, 0.0])[1])
-    n_l, ms_l, pairs_l = prof_acc[dom]
-    avg_ms = ms_l / max(n_l, 1)
-    pairs_per_launch = pairs_l / max(n_l, 1)
-    achieved = FLOPS_PER_PAIR * pairs_per_launch / (avg_ms * 1e-3) / 1e12
-    kname, kp = pair_kinds[dom]
-    gps = pairs_per_launch / (avg_ms * 1e-3)
-    issue_peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12   # T FP32-pipe ops/s
-    if kp == "fp64":
-        roofline = {"bound": "alu", "kernel": kname, "achieved": round(achieved, 3),
-                    "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s", "frac": round(achieved / FP64_NOMINAL_TFLOPS, 4),
-                    "peak_source": "nominal dense FP64 of the part (1.25 TFLOP/s)"}
-    else:
-        ops = DF64_OPS_PER_PAIR if kp == "df64" else F32_OPS_PER_PAIR
-        ach = ops * gps / 1e12
-        roofline = {"bound": "alu", "kernel": kname, "achieved": round(ach, 3), "peak": round(issue_peak, 2),
-                    "unit": "T FP32-pipe ops/s", "frac": round(ach / issue_peak, 4),
-                    "ops_per_pair": ops,
-                    "peak_source": "FP32 pipes: 152 SMs x 128 lanes x 2070 MHz, one op per lane per clock",
-                    "fp64_class_tflops_at_18_flops_per_pair": round(achieved, 3)}
+    prof_acc["_steps"] = args.steps
+    # full operator applications per step, from the pair work the library
+    # recorded (the velocity's 4096 targets add a small fraction)
+    pair_units = sum(prof_acc.get(k, [0, 0.0, 0.0])[2] for k in (0, 1, 2))
+    result["applications"] = int(round(pair_units / args.steps / float(geom.n_nodes) ** 2))
+    peaks = measured_peaks()
+    rooflines = kernel_rooflines(S, prof_acc, peaks)
+    dom = max(rooflines, key=lambda r: r["ms_per_step"] if r["candidate"] else -1.0)
+    roofline = dict(dom)
+    roofline.pop("candidate", None)
     traffic = None
-    if args.workload == "pipe1000" and kp in tuned:
-        traffic = MEASURED_TRAFFIC.get((kname, *tuned[kp]["shape"]))
-    roofline.update({"traffic": traffic, "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, "
-                     "one capture of this kernel shape on this workload" if traffic else None,
-                     "gpairs_per_s": round(gps / 1e9, 2), "avg_launch_ms": round(avg_ms, 4),
-                     "launches": n_l, "flops_per_pair": FLOPS_PER_PAIR})
+    if args.workload == "pipe1000":
+        key = (dom["kernel"],) + tuple(tuned.get(dom.get("precision"), {}).get("shape", ()))
+        traffic = MEASURED_TRAFFIC.get(key)
+    roofline["traffic"] = traffic
+    roofline["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture of this kernel "
+                                  "shape on this workload" if traffic else
+                                  "no ncu capture of this kernel as it now stands")
     phases = {}
-    names = {0: "pairs_fp64", 1: "pairs_fp32", 2: "pairs_df64", 3: "epilogue", 4: "bd_apply", 5: "arnoldi",
-             6: "bd_setup"}
-    for k, (n, ms, units) in prof_acc.items():
+    for k, (n, ms, units) in ((k, v) for k, v in prof_acc.items() if isinstance(k, int)):
         if n:
-            phases[names[k]] = {"launches": n, "ms": round(ms / args.steps, 2)}
+            phases[PROF_NAMES[k]] = {"launches": n, "ms": round(ms / args.steps, 2)}
     cfg = workload_config(args.workload)
     cfg.update({"precision": prec_name, "restart": restart, "targets": args.targets,
                 "pc": {"bd": "block-diagonal (right)",
                        "twogrid": f"two-grid, coarse = every {args.coarsen}th node (flexible GMRES, right)"}[pc_name],
-                "l2": "working set (block inverses and factors > 2.6 GB, Krylov basis) exceeds L2; no flush",
+                "l2": "working set (coarse factors, block inverses, Krylov basis) exceeds L2; no flush",
                 "pair_shapes": tuned or "defaults",
                 "parallelism": f"replicas x{world}"})
     value = ms_step / 1e3
@@ -543,18 +605,227 @@ def main():
             "data": "synthetic", "config": cfg,
             "solve": {"iters": result.get("iters"), "true_relres": result.get("relres"),
                       "status": result.get("code"), "solves_per_s_all_gpus": round(world / value, 4)},
-            "phases_ms_per_step": phases, "roofline": roofline, "clocks": clk, "gpu_launches": launches,
+            "phases_ms_per_step": phases, "roofline": roofline,
+            "kernels": [{k: v for k, v in r.items() if k != "candidate"} for r in rooflines],
+            "clocks": clk, "gpu_launches": launches,
             "e2e": ({"value": round(e2e_s, 4), "unit": "s", "h2d_bytes_per_step": h2d,
                      "d2h_bytes_per_step": d2h} if e2e_s is not None else None)}
     if not args.no_cpu_baseline and world == 1:
-        iters = result.get("iters") or 1
-        ob = oracle_sample(geom, iters, budget_s=15.0)
-        line["cpu_baseline"] = {"value": round(ob["est_time_to_solution_s"], 1), "unit": "s",
-                                "cores": ob["cores"], "kind": "oracle",
-                                "sample": f"{ob['sample_rows']} random rows of A sigma (numpy FP64, "
-                                          f"{ob['pairs_per_s']/1e6:.1f} Mpairs/s) in {ob['sample_s']:.1f} s, "
-                                          f"extrapolated to {iters} full operator applications"}
+        o = cpu_baseline_operator_rate(args.workload, 15.0)
+        apps = result.get("applications") or (result.get("iters") or 0) + 2
+        line["cpu_baseline"] = {
+            "value": round(apps * o["matvec_s"], 1), "unit": "s", "cores": o["cores"], "kind": "oracle",
+            "estimate": True,
+            "sample": f"{o['rows']} random rows of A sigma on {o['cores']} host cores in {o['busy_s']:.1f} s "
+                      f"(numpy FP64, {o['pairs_per_s'] / 1e6:.1f} Mpairs/s): one operator application "
+                      f"{o['matvec_s']:.1f} s, times the {apps} operator applications of this two-grid flexible "
+                      f"GMRES solve (same method; the oracle's coarse setup not counted: a lower bound)"}
+    if args.sub_records and world == 1 and args.workload == "pipe1000":
+        line["sub_records"] = sub_records(args, S, torch, dev, stream)
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# Roofline of each kernel class timed inside the step
+# ---------------------------------------------------------------------------
+
+PROF_NAMES = {0: "pairs_fp64", 1: "pairs_fp32", 2: "pairs_df64", 3: "epilogue", 4: "precond_apply",
+              5: "arnoldi", 6: "precond_setup", 7: "lu_gemm", 8: "lu_panel", 9: "coarse_solve"}
+FP32_FLOP_PEAK = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12   # TFLOP/s, FMA = 2
+FP32_ISSUE_PEAK = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12     # T FP32-pipe ops/s
+
+
+def measured_peaks():
+    """MEASURED_PEAKS.json (driver-written on this pool), else the profiling
+    recipe's fallback figures."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
+                "source": "of measured (MEASURED_PEAKS.json)"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "source": "of fallback (profiling recipe)"}
+
+
+def kernel_rooflines(S, prof_acc, peaks):
+    """One entry per kernel class with recorded launches: its share of the
+    step and its algorithmic work per launch against the bound that limits
+    it. Pair kernels: 18 flop per pair (FMA = 2) against the FP32 CUDA-core
+    FLOP peak (152 SMs x 128 lanes x 2 x 2070 MHz = 80.5 TFLOP/s) and, for
+    the FP64-class kernels, the multiple of the part's nominal FP64 rate;
+    the double-float kernel's FP32-pipe issue use is kept separately. The
+    coarse LU's trailing products: 2 M N K flop against the FP32 CUDA-core
+    peak. The coarse solve: bytes of the factors read per apply against the
+    HBM copy bandwidth."""
+    out = []
+    steps = max(1, prof_acc.get("_steps", 1))
+    for kind, (n, ms, units) in sorted((k, v) for k, v in prof_acc.items() if isinstance(k, int)):
+        if n == 0 or ms <= 0:
+            continue
+        name = PROF_NAMES[kind]
+        sec = ms * 1e-3
+        r = {"class": name, "launches": n, "ms_per_step": round(ms / steps, 2), "avg_launch_ms": round(ms / n, 4),
+             "candidate": kind not in (S.STOKES_PROF_BD_APPLY, S.STOKES_PROF_BD_SETUP)}
+        if kind in (S.STOKES_PROF_PAIRS_FP64, S.STOKES_PROF_PAIRS_FP32, S.STOKES_PROF_PAIRS_DF64):
+            gps = units / sec
+            ach = FLOPS_PER_PAIR * gps / 1e12
+            kname = {0: "k_dlp_pairs_f64", 1: "k_dlp_pairs_f32", 2: "k_dlp_pairs_df64"}[kind]
+            r.update({"kernel": kname, "precision": {0: "fp64", 1: "fp32", 2: "df64"}[kind], "bound": "alu",
+                      "achieved": round(ach, 3), "peak": round(FP32_FLOP_PEAK, 2), "unit": "TFLOP/s",
+                      "frac": round(ach / FP32_FLOP_PEAK, 4), "gpairs_per_s": round(gps / 1e9, 2),
+                      "flops_per_pair": FLOPS_PER_PAIR,
+                      "peak_source": "FP32 CUDA cores: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)"})
+            if kind != S.STOKES_PROF_PAIRS_FP32:
+                r["fp64_nominal_multiple"] = round(ach / FP64_NOMINAL_TFLOPS, 3)
+            if kind == S.STOKES_PROF_PAIRS_DF64:
+                issue = DF64_OPS_PER_PAIR * gps / 1e12
+                r["fp32_issue"] = {"achieved": round(issue, 2), "peak": round(FP32_ISSUE_PEAK, 2),
+                                   "unit": "T FP32-pipe ops/s", "frac": round(issue / FP32_ISSUE_PEAK, 4),
+                                   "ops_per_pair": DF64_OPS_PER_PAIR}
+        elif kind == S.STOKES_PROF_LU_GEMM:
+            ach = units / sec / 1e12
+            r.update({"kernel": "k_sgemm128", "bound": "alu", "achieved": round(ach, 2),
+                      "peak": round(FP32_FLOP_PEAK, 2), "unit": "TFLOP/s", "frac": round(ach / FP32_FLOP_PEAK, 4),
+                      "peak_source": "FP32 CUDA cores (derived)"})
+        elif kind in (S.STOKES_PROF_COARSE_SOLVE, S.STOKES_PROF_BD_APPLY, S.STOKES_PROF_ARNOLDI):
+            gbs = units / sec / 1e9
+            kname = {S.STOKES_PROF_COARSE_SOLVE: "k_lu_solve_persistent", S.STOKES_PROF_BD_APPLY: "(preconditioner apply)",
+                     S.STOKES_PROF_ARNOLDI: "k_dot_partial + k_orth_update"}[kind]
+            r.update({"kernel": kname, "bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"],
+                      "unit": "GB/s", "frac": round(gbs / peaks["hbm_gbs"], 4), "peak_source": peaks["source"]})
+        elif kind == S.STOKES_PROF_LU_PANEL:
+            r.update({"kernel": "k_panel_lu32", "bound": "latency", "achieved": round(units / sec, 1),
+                      "unit": "columns/s", "note": "two grid barriers per column"})
+        else:
+            r.update({"kernel": name})
+        out.append(r)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Sub-records: the other configurations, measured once per run after the
+# timed region (each with its own timing and its error against the oracle)
+# ---------------------------------------------------------------------------
+
+def _events(torch, stream):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _handle(S, geom, dev, torch, sptr):
+    d = lambda a: torch.tensor(np.ascontiguousarray(a).reshape(-1), dtype=torch.float64, device=dev)
+    return S.stokes_geometry_create(d(geom.nodes), d(geom.normals), d(geom.weights), d(geom.curvature),
+                                    geom.offsets, geom.n_comp, geom.outer_comp,
+                                    np.ascontiguousarray(geom.centres).reshape(-1), sptr)
+
+
+def _rel(a, b):
+    a = np.asarray(a).reshape(-1)
+    b = np.asarray(b).reshape(-1)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def small_config_records(args, S, torch, dev, stream):
+    """The 1152-node pipe (10 pores x 64 nodes + 512-node wall): the plain
+    FP64 block-diagonal GMRES(50) solve to 1e-10, and the mixed-precision
+    solve (FP32 inner GMRES(30), FP64 refinement to 1e-8). Each is timed on
+    the device (handle, setup, solve, velocity at 4096 targets; mean of 5
+    after 2 warm-ups) and compared with the oracle's dense FP64 solution and
+    its velocity at the same targets."""
+    import stokes_inputs as si
+    geom = si.cached_geometry("pipe10", 0)
+    f_h = si.pipe_bc(geom).reshape(-1)
+    T_h = si.interior_targets(geom, 4096, min_dist=0.05, seed=3)
+    sptr = stream.cuda_stream
+    f = torch.tensor(f_h, device=dev)
+    tg = torch.tensor(T_h.reshape(-1), device=dev)
+    u = torch.empty(T_h.size, dtype=torch.float64, device=dev)
+    ref = cpu_baseline_small_solve(geom, f_h, tol=1e-10, restart=50)
+    u_ref = cpu_baseline_velocity(geom, ref["x_dense"], T_h)
+    out = {}
+    for name, prec, tol, restart in (("config1_fp64_block_diagonal", S.STOKES_FP64, 1e-10, 50),
+                                     ("config3_mixed_fp32_inner_fp64_refinement", S.STOKES_MIXED_IR, 1e-8, 30)):
+        times, res = [], None
+        for rep in range(7):
+            sig = torch.zeros_like(f)
+            a, b = _events(torch, stream)
+            torch.cuda.synchronize()
+            a.record(stream)
+            h = _handle(S, geom, dev, torch, sptr)
+            try:
+                S.stokes_precond_setup(h, S.STOKES_PC_BLOCKDIAG)
+                res = S.stokes_gmres_solve(h, f, sig, tol=tol, restart=restart, max_iter=5000, precision=prec)
+                S.stokes_eval_velocity(h, sig, tg, u, S.STOKES_FP64)
+            finally:
+                S.stokes_geometry_destroy(h)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if rep >= 2:
+                times.append(a.elapsed_time(b))
+        code, iters, relres, _ = res
+        x = sig.cpu().numpy()
+        out[name] = {"workload": "porous pipe, 10 pores x 64 nodes + 512-node wall (N=1152, 2304 unknowns)",
+                     "method": ("block-diagonal GMRES(50), FP64" if prec == S.STOKES_FP64 else
+                                "block-diagonal, FP32 inner GMRES(30) in FP64 iterative refinement"),
+                     "tol": tol, "time_to_solution_s": round(float(np.mean(times)) / 1e3, 5),
+                     "iters": iters, "true_relres": relres, "status": code,
+                     "density_rel_err_vs_oracle": _rel(x, ref["x_dense"]),
+                     "velocity_rel_err_vs_oracle_4096_targets": _rel(u.cpu().numpy(), u_ref),
+                     "timing": "CUDA events around handle creation, setup, solve and velocity; mean of 5 after 2"}
+    out["config1_cpu_oracle"] = {"gmres_s": round(ref["gmres_s"], 3), "iters": ref["iters"],
+                                 "relres": ref["relres"], "dense_lu_s": round(ref["dense_lu_s"], 3), "cores": 1,
+                                 "kind": "oracle",
+                                 "sample": "full oracle solve (dense assembly, block-diagonal LU, GMRES(50) to 1e-10)"}
+    return out
+
+
+def plain_bd_baseline(args, S, torch, dev, stream):
+    """Plain FP64 block-diagonal GMRES on the 136,192-node pipe (the paper's
+    baseline preconditioner, Sec. 4.1; unrestarted, right-preconditioned,
+    native FP64 operator). A 10-iteration pilot gives the time per
+    iteration; the measured solve then runs to 1e-8 or until its iteration
+    cap, chosen so that it takes about --baseline-budget seconds (at most
+    2000 iterations, the paper's cap at 826 pores)."""
+    import stokes_inputs as si
+    geom = si.cached_geometry("pipe1000", 0)
+    f = torch.tensor(si.pipe_bc(geom).reshape(-1), device=dev)
+    sptr = stream.cuda_stream
+    h = _handle(S, geom, dev, torch, sptr)
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.stokes_precond_setup(h, S.STOKES_PC_BLOCKDIAG)
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        sig = torch.zeros_like(f)
+        t0 = time.perf_counter()
+        S.stokes_gmres_solve(h, f, sig, tol=1e-8, restart=10, max_iter=10, precision=S.STOKES_FP64)
+        torch.cuda.synchronize()
+        per_iter = (time.perf_counter() - t0) / 10.0
+        cap = int(max(10, min(2000, args.baseline_budget / per_iter)))
+        sig.zero_()
+        t0 = time.perf_counter()
+        code, iters, relres, _ = S.stokes_gmres_solve(h, f, sig, tol=1e-8, restart=cap, max_iter=cap,
+                                                      precision=S.STOKES_FP64)
+        torch.cuda.synchronize()
+        solve_s = time.perf_counter() - t0
+    finally:
+        S.stokes_geometry_destroy(h)
+    return {"workload": workload_config("pipe1000")["workload"],
+            "method": "block-diagonal (Sec. 4.1) right-preconditioned GMRES, unrestarted, FP64 operator",
+            "setup_s": round(setup_s, 3), "solve_s": round(solve_s, 2), "iters": iters, "iteration_cap": cap,
+            "true_relres": relres, "status": code, "converged": code == S.STOKES_OK,
+            "s_per_iter": round(solve_s / max(1, iters), 4),
+            "timing": "host clock around synchronised calls, measured once per run after the timed region"}
+
+
+def sub_records(args, S, torch, dev, stream):
+    out = {}
+    out.update(small_config_records(args, S, torch, dev, stream))
+    if args.baseline_budget > 0:
+        out["baseline_plain_fp64_block_diagonal"] = plain_bd_baseline(args, S, torch, dev, stream)
+    return out
 
 
 if __name__ == "__main__":

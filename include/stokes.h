@@ -223,6 +223,13 @@ int stokes_eval_velocity(stokes_geom* g, const double* sigma, const double* targ
  *   BD_APPLY   bytes: every block inverse / factor read once, v in, z out
  *   ARNOLDI    bytes of one CGS2 step: 4 (j + 1) + 4 vectors of 2N doubles
  *   BD_SETUP   flops: (2/3) m^3 per block, 2 m^3 where the inverse is formed
+ *   LU_GEMM    flops 2 M N K of the trailing-update products of the two-grid
+ *              coarse LU (and of its explicit inverse)
+ *   LU_PANEL   columns factorised by the coarse LU's panel kernels
+ *   COARSE_SOLVE bytes of the coarse factors or inverse read per apply (4 m^2)
+ * BD_APPLY covers a whole preconditioner apply; for the two-grid
+ * preconditioner its units are the bytes of the coarse factors, the
+ * transfer matrices and the pore blocks read once, plus v in and z out.
  * Any output pointer may be NULL. */
 enum stokes_prof_kind {
   STOKES_PROF_PAIRS_FP64 = 0,
@@ -231,7 +238,10 @@ enum stokes_prof_kind {
   STOKES_PROF_EPILOGUE = 3,
   STOKES_PROF_BD_APPLY = 4,
   STOKES_PROF_ARNOLDI = 5,
-  STOKES_PROF_BD_SETUP = 6
+  STOKES_PROF_BD_SETUP = 6,
+  STOKES_PROF_LU_GEMM = 7,
+  STOKES_PROF_LU_PANEL = 8,
+  STOKES_PROF_COARSE_SOLVE = 9
 };
 int stokes_profile_enable(stokes_geom* g, int on);
 int stokes_profile_read(stokes_geom* g, int kind, int64_t* launches, double* total_ms,
@@ -239,24 +249,32 @@ int stokes_profile_read(stokes_geom* g, int kind, int64_t* launches, double* tot
 
 /* y = A sigma in FP64 without a handle and without allocating GPU memory.
  * The paper has no counterpart: this entry point exists for callers that
- * cannot allocate (inside a CUDA graph capture, under an allocator that owns
- * the whole device, on paths where an allocation's device synchronisation
- * is not allowed). It computes the same operator as stokes_matvec with
- * STOKES_FP64, reading the boundary arrays directly instead of a handle.
+ * cannot allocate, such as code under an allocator that owns the whole
+ * device (a framework memory pool, an embedded runtime with a fixed arena)
+ * or on paths where an allocation's implicit device synchronisation is not
+ * allowed. It computes the same operator as stokes_matvec with STOKES_FP64,
+ * reading the boundary arrays directly instead of a handle.
  *   nodes, normals [2N], weights, curvature [N], sigma, y [2N]: DEVICE arrays
+ *   of the current device (or managed memory)
  *   offsets [n_comp+1], centres [2 n_comp] (the completion centres; the
- *   wall's entry is ignored): HOST arrays; n_comp, outer_comp as in
- *   stokes_geometry_create; stream: cudaStream_t (NULL = legacy stream).
+ *   wall's entry is ignored): HOST arrays, copied into the scratch array by
+ *   cudaMemcpyAsync on `stream`: pageable memory is read before the call
+ *   returns, pinned memory when the copy runs, so keep pinned arrays
+ *   unchanged until the stream has passed this call;
+ *   n_comp, outer_comp as in stokes_geometry_create;
+ *   stream: cudaStream_t (NULL = legacy stream).
  * Its scratch (offsets, centres, moments, split partial sums) lives in one
  * 32 MiB file-scope device array that every GPU loading the library keeps
  * until exit; problems that need more (about 2 million nodes and up) are
- * rejected with STOKES_EINVAL before anything runs, as are host arrays for
- * the device arguments and the offsets errors of stokes_geometry_create.
- * All calls on a device share that array and leave their contents in it;
- * every call writes all it reads, so nothing needs clearing, but two calls
- * that overlap on the GPU race and give wrong results. The first call on a
- * device looks up the array's address (cudaGetSymbolAddress) with that
- * device current; make it before any stream capture. Asynchronous on
+ * rejected with STOKES_EINVAL before anything runs, as are host arrays or
+ * another device's arrays for the device arguments and the offsets errors
+ * of stokes_geometry_create. All calls on a device share that array and
+ * leave their contents in it; every call writes all it reads, so nothing
+ * needs clearing, but two calls that overlap on the GPU race and give wrong
+ * results. The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress) with that device current and keeps it for the
+ * life of the process (cudaDeviceReset between calls is not supported);
+ * make that first call before any stream capture. Asynchronous on
  * `stream`; returns STOKES_OK, STOKES_EINVAL or STOKES_ECUDA and sets no
  * stokes_last_error() message. */
 int stokes_matvec_noalloc(const double* nodes, const double* normals, const double* weights,
@@ -371,6 +389,15 @@ int stokes_batch_solve(stokes_geom* const* geoms, int n_geoms, int n_rhs, const 
  * kernels that return early because a solve already converged count too).
  * Synchronises the device; -1 on error. */
 int64_t stokes_kernel_launches(void);
+
+/* y[i] = 1 / x[i] as the FP64 pair kernel computes it (the paper has no
+ * counterpart; exposed so that tests can check it against IEEE division):
+ * the hardware's approximate reciprocal (PTX rcp.approx.ftz.f64) refined
+ * by two Newton-Raphson steps y <- y + y (1 - x y): within about one ulp
+ * for normal positive x; non-finite for x = 0. x, y: DEVICE arrays of n doubles
+ * (may alias). Asynchronous on `stream` (NULL = legacy stream).
+ * Errors: STOKES_EINVAL, STOKES_ECUDA. */
+int stokes_rcp_f64(const double* x, double* y, int64_t n, void* stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* stokes_last_error(void);

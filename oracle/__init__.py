@@ -4,3 +4,4 @@ from .stokes_oracle import (  # noqa: F401
     assemble, moments, apply_rows, matvec, velocity, BlockDiagonal, gmres,
     solve_dense, solve_gmres, trig_interpolation, coarse_geometry, TwoGrid, fgmres,
 )
+from . import learned_coarse  # noqa: F401,E402

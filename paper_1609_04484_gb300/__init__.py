@@ -24,11 +24,12 @@ __all__ = [
     "stokes_gmres_solve", "stokes_eval_velocity", "stokes_last_error", "Geometry",
     "stokes_profile_enable", "stokes_profile_read", "STOKES_PROF_PAIRS_FP64", "STOKES_PROF_PAIRS_FP32",
     "STOKES_PROF_PAIRS_DF64", "STOKES_PROF_EPILOGUE", "STOKES_PROF_BD_APPLY", "STOKES_PROF_ARNOLDI",
-    "STOKES_PROF_BD_SETUP", "stokes_kernel_launches", "stokes_matvec_noalloc",
+    "STOKES_PROF_BD_SETUP", "STOKES_PROF_LU_GEMM", "STOKES_PROF_LU_PANEL", "STOKES_PROF_COARSE_SOLVE",
+    "stokes_kernel_launches", "stokes_matvec_noalloc",
     "stokes_pair_shape_count", "stokes_pair_shape_info", "stokes_set_pair_shape", "stokes_get_pair_shape",
     "stokes_autotune", "stokes_tune_cache_insert", "stokes_tune_cache_lookup", "stokes_tune_cache_clear",
     "stokes_tune_cache_save", "stokes_tune_cache_load", "stokes_batch_matvec", "stokes_batch_solve",
-    "stokes_precond_setup_twogrid_ex", "STOKES_TG_COARSE_AUTO", "STOKES_TG_COARSE_INVERSE", "STOKES_TG_COARSE_LU",
+    "stokes_precond_setup_twogrid_ex", "stokes_rcp_f64", "STOKES_TG_COARSE_AUTO", "STOKES_TG_COARSE_INVERSE", "STOKES_TG_COARSE_LU",
 ]
 
 STOKES_OK, STOKES_EINVAL, STOKES_ENOMEM, STOKES_ECUDA = 0, -1, -2, -3
@@ -38,7 +39,8 @@ STOKES_PC_NONE, STOKES_PC_BLOCKDIAG, STOKES_PC_TWOGRID = 0, 1, 2
 STOKES_PC_RIGHT, STOKES_PC_LEFT = 0, 1
 STOKES_TG_COARSE_AUTO, STOKES_TG_COARSE_INVERSE, STOKES_TG_COARSE_LU = 0, 1, 2
 (STOKES_PROF_PAIRS_FP64, STOKES_PROF_PAIRS_FP32, STOKES_PROF_PAIRS_DF64, STOKES_PROF_EPILOGUE,
- STOKES_PROF_BD_APPLY, STOKES_PROF_ARNOLDI, STOKES_PROF_BD_SETUP) = range(7)
+ STOKES_PROF_BD_APPLY, STOKES_PROF_ARNOLDI, STOKES_PROF_BD_SETUP, STOKES_PROF_LU_GEMM, STOKES_PROF_LU_PANEL,
+ STOKES_PROF_COARSE_SOLVE) = range(10)
 
 _PKG = pathlib.Path(__file__).resolve().parent
 library_path = _PKG / "lib" / "libstokes.so"
@@ -85,6 +87,7 @@ def _load():
         "stokes_tune_cache_load": (I, [ctypes.c_char_p, ctypes.POINTER(I)]),
         "stokes_batch_matvec": (I, [P, I, I, P, P, I]),
         "stokes_batch_solve": (I, [P, I, I, P, D, I, I, I, P, P, P, P]),
+        "stokes_rcp_f64": (I, [P, P, I64, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -221,12 +224,17 @@ def stokes_matvec_noalloc(nodes, normals, weights, curvature, offsets, n_comp, o
                           stream=None):
     """y = A sigma in FP64 without a handle and without allocating GPU memory
     (for callers that cannot allocate). nodes, normals, weights, curvature,
-    sigma and y must be device arrays (torch CUDA tensors); offsets and
-    centres are host arrays. Returns the status code (STOKES_EINVAL for host
-    arrays or a problem beyond the fixed scratch size)."""
+    sigma and y must be device arrays (torch CUDA tensors) of the current
+    device; offsets (n_comp + 1 entries) and centres (2 n_comp) are host
+    arrays. Returns the status code (STOKES_EINVAL for host arrays or a
+    problem beyond the fixed scratch size)."""
     off = np.ascontiguousarray(offsets, dtype=np.int64)
     cen = np.ascontiguousarray(centres, dtype=np.float64)
-    N = int(off[-1])
+    if off.ndim != 1 or off.size != int(n_comp) + 1:
+        raise ValueError(f"offsets must have n_comp + 1 = {int(n_comp) + 1} entries, got {off.size}")
+    if cen.size < 2 * int(n_comp):
+        raise ValueError(f"centres must have 2 n_comp = {2 * int(n_comp)} entries, got {cen.size}")
+    N = int(off[int(n_comp)])
     st = None if stream is None else ctypes.c_void_p(int(stream))
     return int(lib.stokes_matvec_noalloc(_ptr(nodes, count=2 * N), _ptr(normals, count=2 * N),
                                          _ptr(weights, count=N), _ptr(curvature, count=N),
@@ -328,6 +336,13 @@ def stokes_batch_solve(handles, n_rhs, f, sigma, tol=1e-8, restart=50, max_iter=
     _check(lib.stokes_batch_solve(_ptr_array(handles), len(handles), int(n_rhs), _ptr_array(f, ns), float(tol),
                                   int(restart), int(max_iter), int(precision), _ptr_array(sigma, ns), it, rr, st))
     return list(it), list(rr), list(st)
+
+
+def stokes_rcp_f64(x, y, stream=None):
+    """y = 1 / x by the FP64 pair kernel's Newton reciprocal (device tensors)."""
+    n = x.numel() if hasattr(x, "numel") else x.size
+    st = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(lib.stokes_rcp_f64(_ptr(x, count=n), _ptr(y, count=n), ctypes.c_int64(n), st))
 
 
 class Geometry:

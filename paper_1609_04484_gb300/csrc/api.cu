@@ -265,7 +265,7 @@ int64_t stokes_kernel_launches(void) {
   try {
     return (int64_t)(stokes::launches_geometry() + stokes::launches_dlp_f64() + stokes::launches_dlp_f32() +
                      stokes::launches_dlp_df64() + stokes::launches_bd() + stokes::launches_bd_trsv() + stokes::launches_bd_inv32() + stokes::launches_twogrid() +
-                     stokes::launches_gmres() + stokes::launches_batch());
+                     stokes::launches_gmres() + stokes::launches_batch() + stokes::launches_noalloc());
   } catch (...) {
     return -1;
   }
@@ -292,6 +292,16 @@ int stokes_batch_solve(stokes_geom* const* geoms, int n_geoms, int n_rhs, const 
     for (int k = 0; k < n_geoms; ++k) gs[k] = &handle(geoms[k]);
     stokes::batch_solve(gs.data(), n_geoms, n_rhs, f, tol, restart, max_iter, precision, sigma, iters, relres,
                         status);
+  });
+}
+
+int stokes_rcp_f64(const double* x, double* y, int64_t n, void* stream) {
+  return guarded([&] {
+    stokes::require(n >= 0, "n must be >= 0");
+    if (n == 0) return;
+    stokes::require(x && y && stokes::is_device_pointer(x) && stokes::is_device_pointer(y),
+                    "x and y must be device arrays");
+    stokes::rcp_newton_apply(x, y, n, (cudaStream_t)stream);
   });
 }
 

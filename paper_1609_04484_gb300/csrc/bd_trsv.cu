@@ -141,7 +141,7 @@ void lu_solve_persistent(Geom& g, const T* A, int64_t m, const int* perm, const 
   }
   // count and generation restart at zero; the error word (slot 2) is sticky
   STOKES_CUDA(cudaMemsetAsync(b.barrier.get(), 0, 2 * sizeof(unsigned), g.stream));
-  Barrier bar{b.barrier.get(), b.barrier.get() + 1, (int*)(b.barrier.get() + 2)};
+  Barrier bar{b.barrier.get(), b.barrier.get() + 1, (int*)(b.barrier.get() + 2), gsync::spin_limit()};
   void* args[] = {(void*)&A, (void*)&m, (void*)&perm, (void*)&v, (void*)&work, (void*)&z, (void*)&bar,
                   (void*)&done};
   STOKES_CUDA(cudaLaunchCooperativeKernel((const void*)k_lu_solve_persistent<T>, dim3(grid), dim3(kThreads), args,

@@ -25,6 +25,22 @@ inline void pair_launch_shape(int64_t N, int64_t T, int tb, int tile, int& split
   splits = (int)((N + chunk - 1) / chunk);
 }
 
+// Reciprocal of a positive double by Newton-Raphson iteration
+// y <- y + y (1 - a y), each step squaring the relative error, from the
+// hardware's approximate double reciprocal (PTX rcp.approx.ftz.f64, about
+// single-precision accurate): two steps bring it within about one ulp of
+// 1 / a. Four FP64 FMAs and one special-function op replace the FP64
+// division's longer sequence on the FP64 pipe. a = +inf (and anything the
+// approximation maps to 0) gives 0; a = 0 gives a non-finite value.
+__device__ __forceinline__ double rcp_newton(double a) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
+  double e = fma(-a, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-a, y, 1.0);
+  return fma(y, e, y);
+}
+
 // ---------------------------------------------------------------------------
 // Double-float arithmetic: a value is hi + lo with |lo| <= ulp(hi) (up to a
 // few ulps where normalisation is skipped). Error-free transformations:

@@ -58,7 +58,7 @@ k_dlp_pairs_f64(int64_t N, const double4_32a* __restrict__ src, const double2* _
         const double rx = x[t].x - s.x, ry = x[t].y - s.y;
         double r2 = fma(rx, rx, ry * ry);
         r2 = (t0 + q == iself[t]) ? 1.0 : r2;  // r = 0 there, so the pair contributes 0
-        const double inv = 1.0 / r2;
+        const double inv = dlp::rcp_newton(r2);
         const double d = fma(rx, s.z, ry * s.w);
         const double e = fma(rx, sg.x, ry * sg.y);
         const double c = (d * inv) * (e * inv);
@@ -122,6 +122,20 @@ void dlp_apply_f64(Geom& g, const double2* sigma, double2* y, bool boundary, con
   const int pq = g.prof.begin(kProfEpilogue, (double)g.M * (double)T, g.stream);
   dlp::launch_epilogue<dlp::kCompF64>(g, T, splits, boundary, targets, sigma, y, done);
   g.prof.end(pq, g.stream);
+}
+
+namespace {
+__global__ void k_rcp_newton(const double* __restrict__ x, double* __restrict__ y, int64_t n) {
+  count_launch();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = dlp::rcp_newton(x[i]);
+}
+}  // namespace
+
+void rcp_newton_apply(const double* x, double* y, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  k_rcp_newton<<<(unsigned)imin64((n + 255) / 256, 152 * 8), 256, 0, s>>>(x, y, n);
+  STOKES_LAUNCHED();
 }
 
 }  // namespace stokes

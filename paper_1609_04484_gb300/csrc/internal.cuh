@@ -131,7 +131,8 @@ struct Krylov {
 // the handle's stream while enabled; read back (synchronising) on demand.
 enum ProfKind {
   kProfPairsF64 = 0, kProfPairsF32 = 1, kProfPairsDF64 = 2, kProfEpilogue = 3,
-  kProfBdApply = 4, kProfArnoldi = 5, kProfBdSetup = 6, kProfKinds = 7
+  kProfBdApply = 4, kProfArnoldi = 5, kProfBdSetup = 6, kProfLuGemm = 7, kProfLuPanel = 8,
+  kProfCoarseSolve = 9, kProfKinds = 10
 };
 struct ProfEntry {
   cudaEvent_t a, b;
@@ -269,6 +270,7 @@ unsigned long long launches_bd_inv32();
 unsigned long long launches_twogrid();
 unsigned long long launches_gmres();
 unsigned long long launches_batch();
+unsigned long long launches_noalloc();
 
 // ---- geometry.cu ----
 // component moments (lambda_x, lambda_y, xi, s0) of sigma into `out`
@@ -280,6 +282,9 @@ void moments_f64(Geom& g, const double2* sigma, const int* done, double4_32a* ou
 // interior velocity at T targets (boundary=false). All pointers device.
 void dlp_apply_f64(Geom& g, const double2* sigma, double2* y, bool boundary,
                    const double2* targets, int64_t T, const int* done);
+
+// y[i] = the FP64 pair kernel's reciprocal of x[i] (device arrays)
+void rcp_newton_apply(const double* x, double* y, int64_t n, cudaStream_t s);
 
 // pair kernels alone (into g.part; returns the number of source splits)
 int pairs_f64(Geom& g, const double2* sigma, const double2* targets, int64_t T, bool boundary, PairShape sh,

@@ -1,16 +1,16 @@
 // stokes_matvec_noalloc: y = A sigma (the FP64 double-layer operator) for
 // callers that cannot allocate GPU memory.
 //
-// Some callers cannot call cudaMalloc at all: code running inside a CUDA
-// graph capture, under an allocator that owns every byte of the device (a
-// framework memory pool, an embedded runtime with a fixed arena), or on a
-// real-time path where an allocation's implicit device synchronisation is not
-// allowed. This variant of the operator does everything the normal one does
-// (per-component moments, the tiled pair sum split over sources, the
-// diagonal, jump, completion and wall terms) without a handle and without
-// allocating: the arrays it needs besides the caller's inputs and outputs
-// live in one file-scope device array, kScratchBytes long, that every GPU
-// which loads the library keeps until the process exits.
+// Some callers cannot call cudaMalloc: code running under an allocator that
+// owns every byte of the device (a framework memory pool, an embedded
+// runtime with a fixed arena), or on a real-time path where an
+// allocation's implicit device synchronisation is not allowed. This variant
+// of the operator does everything the normal one does (per-component
+// moments, the tiled pair sum split over sources, the diagonal, jump,
+// completion and wall terms) without a handle and without allocating: the
+// arrays it needs besides the caller's inputs and outputs live in one
+// file-scope device array, kScratchBytes long, that every GPU which loads the
+// library keeps until the process exits.
 //
 // The array is shared by all calls on a device and keeps the last call's
 // contents. Every word a call reads is first written by the same call, so
@@ -19,9 +19,11 @@
 //
 // Host code cannot use the array's name as a device address; the first call
 // on each device looks the address up with cudaGetSymbolAddress while that
-// device is current and keeps it. Make that first call outside any stream
-// capture.
+// device is current and keeps it for the life of the process (a
+// cudaDeviceReset between calls is not supported). Make that first call
+// before any stream capture.
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 
 #include "internal.cuh"
@@ -34,7 +36,7 @@ constexpr int kTile = 128;
 
 static __device__ __align__(256) unsigned char g_matvec_scratch[kScratchBytes];
 
-void* g_scratch_addr[kMaxDevices] = {};
+std::atomic<void*> g_scratch_addr[kMaxDevices] = {};
 
 // Layout inside the scratch array (byte offsets, 256-aligned).
 struct Layout {
@@ -67,6 +69,7 @@ __global__ void k_na_moments(const double2* __restrict__ pos, const double2* __r
                              const double* __restrict__ w, const double2* __restrict__ sig,
                              const int64_t* __restrict__ off, const double2* __restrict__ centre,
                              double4_32a* __restrict__ mom) {
+  stokes::count_launch();
   __shared__ double red[4][256];
   const int k = blockIdx.x;
   const double2 c = centre[k];
@@ -96,6 +99,7 @@ __global__ void k_na_moments(const double2* __restrict__ pos, const double2* __r
 __global__ void __launch_bounds__(kTile)
 k_na_pairs(int64_t N, const double2* __restrict__ pos, const double2* __restrict__ nrm, const double* __restrict__ w,
            const double2* __restrict__ sig, int64_t chunk, double2* __restrict__ part) {
+  stokes::count_launch();
   __shared__ double4_32a s_src[kTile];
   __shared__ double2 s_sig[kTile];
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -135,6 +139,7 @@ __global__ void k_na_epilogue(int64_t N, int splits, const double2* __restrict__
                               const double2* __restrict__ sig, const int64_t* __restrict__ off, int n_comp, int outer,
                               const double2* __restrict__ centre, const double4_32a* __restrict__ mom,
                               const double2* __restrict__ part, double2* __restrict__ y) {
+  stokes::count_launch();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   double ax = 0.0, ay = 0.0;
@@ -169,14 +174,17 @@ __global__ void k_na_epilogue(int64_t N, int splits, const double2* __restrict__
   y[i] = make_double2(ax + stokes::kInv4Pi * cx, ay + stokes::kInv4Pi * cy);
 }
 
-// Device memory (or managed) only: the kernels dereference the pointers.
-bool on_device(const void* p) {
+// Device memory (or managed) of the current device only: the kernels
+// dereference the pointers, and another GPU's memory is not reachable
+// without peer access.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -187,33 +195,33 @@ int stokes_matvec_noalloc(const double* nodes, const double* normals, const doub
                           const int64_t* offsets, int n_comp, int outer_comp, const double* centres,
                           const double* sigma, double* y, void* stream) {
   if (!nodes || !normals || !weights || !curvature || !offsets || !centres || !sigma || !y) return STOKES_EINVAL;
-  if (!on_device(nodes) || !on_device(normals) || !on_device(weights) || !on_device(curvature) ||
-      !on_device(sigma) || !on_device(y))
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return STOKES_ECUDA;
+  if (dev < 0 || dev >= kMaxDevices) return STOKES_EINVAL;
+  if (!on_device(nodes, dev) || !on_device(normals, dev) || !on_device(weights, dev) ||
+      !on_device(curvature, dev) || !on_device(sigma, dev) || !on_device(y, dev))
     return STOKES_EINVAL;
   if (n_comp < 1 || outer_comp < 0 || outer_comp >= n_comp) return STOKES_EINVAL;
   if (offsets[0] != 0) return STOKES_EINVAL;
   for (int c = 0; c < n_comp; ++c)
     if (offsets[c + 1] - offsets[c] < 8) return STOKES_EINVAL;
   const int64_t N = offsets[n_comp];
-  // split the sources over CTAs only as far as the scratch array allows
+  // split the sources so the grid holds about four CTAs per SM (152 SMs);
+  // from 77,824 nodes on one split already fills the GPU
   const int64_t tblocks = (N + kTile - 1) / kTile;
-  int64_t splits = std::max<int64_t>(1, std::min<int64_t>((4 * 152 + tblocks - 1) / tblocks, (N + kTile - 1) / kTile));
-  while (splits > 1 && layout(n_comp, N, (int)splits).total > kScratchBytes) --splits;
+  const int64_t want = std::max<int64_t>(1, std::min<int64_t>((4 * 152 + tblocks - 1) / tblocks, tblocks));
+  const int64_t chunk = ((N + want - 1) / want + kTile - 1) / kTile * kTile;
+  const int64_t splits = (N + chunk - 1) / chunk;
   const Layout L = layout(n_comp, N, (int)splits);
   if (L.total > kScratchBytes) return STOKES_EINVAL;  // beyond the fixed scratch array
-  const int64_t chunk = ((N + splits - 1) / splits + kTile - 1) / kTile * kTile;
-  splits = (N + chunk - 1) / chunk;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return STOKES_ECUDA;
-  if (dev >= kMaxDevices) return STOKES_EINVAL;
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_matvec_scratch);
+  void* addr = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!addr) {
+    e = cudaGetSymbolAddress(&addr, g_matvec_scratch);
     if (e != cudaSuccess) return STOKES_ECUDA;
-    g_scratch_addr[dev] = p;
+    g_scratch_addr[dev].store(addr, std::memory_order_release);  // concurrent first calls store the same value
   }
-  unsigned char* base = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  unsigned char* base = static_cast<unsigned char*>(addr);
   auto* d_off = reinterpret_cast<int64_t*>(base + L.off_offsets);
   auto* d_cen = reinterpret_cast<double2*>(base + L.off_centres);
   auto* d_mom = reinterpret_cast<double4_32a*>(base + L.off_moments);
@@ -234,3 +242,7 @@ int stokes_matvec_noalloc(const double* nodes, const double* normals, const doub
 }
 
 }  // extern "C"
+
+namespace stokes {
+unsigned long long launches_noalloc() { return tu_launches(); }
+}  // namespace stokes

@@ -674,8 +674,9 @@ void twogrid_setup(Geom& g, int q, int coarse_mode) {
   for (int64_t k0 = 0; k0 < m; k0 += kNb) {
     const int kb = (int)std::min<int64_t>(kNb, m - k0);
     mark();
+    const int pp = g.prof.begin(kProfLuPanel, (double)kb, s);
     if (coop_grid > 0) {
-      gsync::Barrier bar{t.barrier.get(), t.barrier.get() + 1, (int*)(t.barrier.get() + 2)};
+      gsync::Barrier bar{t.barrier.get(), t.barrier.get() + 1, (int*)(t.barrier.get() + 2), gsync::spin_limit()};
       int64_t k0v = k0;
       int kbv = kb;
       float* pvp = pv.get();
@@ -698,13 +699,16 @@ void twogrid_setup(Geom& g, int q, int coarse_mode) {
                              s>>>(A, m, c, k0 + kb, ivp.get());
       }
     }
+    g.prof.end(pp, s);
     const int64_t rest = m - k0 - kb;
     mark();
     if (rest > 0) {
       k_trsm_row_panel32<<<(unsigned)((rest + 127) / 128), 128, 0, s>>>(A, m, k0, kb);
       // A22 -= L21 U12 (rows and columns from k0 + kb on)
       const int64_t base = k0 + kb;
+      const int pg = g.prof.begin(kProfLuGemm, 2.0 * (double)rest * (double)rest * kb, s);
       sgemm32(s, rest, rest, kb, -1.f, A + k0 * m + base, m, A + base * m + k0, m, 1.f, A + base * m + base, m);
+      g.prof.end(pg, s);
     }
     STOKES_LAUNCHED();
   }
@@ -778,6 +782,7 @@ static void twogrid_apply(Geom& g, const double* r, double* z, const int* done, 
       t.Nc, t.comp_c.get(), g.d_off.get(), t.d_off_c.get(), t.rpart.get(), t.rc.get(), t.rc32.get(), done);
   STOKES_LAUNCHED();
   const int64_t m = 2 * t.Nc;
+  const int pc = g.prof.begin(kProfCoarseSolve, 4.0 * (double)m * (double)m, s);
   if (t.use_lu) {
     lu_solve_persistent<float>(g, t.lu.get(), m, t.perm.get(), t.rc.get(), t.zc.get(), t.work32.get(), done);
   } else {
@@ -786,6 +791,7 @@ static void twogrid_apply(Geom& g, const double* r, double* z, const int* done, 
     k_dense_gemv32_sum<<<(unsigned)std::min<int64_t>(152 * 4, (m + 255) / 256), 256, 0, s>>>(t.gemv_part.get(), m,
                                                                                            t.zc.get(), done);
   }
+  g.prof.end(pc, s);
   STOKES_LAUNCHED();
   k_prolong<<<(unsigned)std::min<int64_t>(152 * 16, (g.N + 7) / 8), 256, 0, s>>>(
       g.N, g.outer, g.comp.get(), g.d_off.get(), t.d_off_c.get(), t.d_ioff.get(), t.interp.get(), r, t.rc.get(),
@@ -796,7 +802,12 @@ static void twogrid_apply(Geom& g, const double* r, double* z, const int* done, 
 
 void precond_apply(Geom& g, const double* v, double* z, const int* done, bool f32) {
   if (g.tg.ready) {
-    const int pb = g.prof.begin(kProfBdApply, 0.0, g.stream);
+    const TwoGrid& t = g.tg;
+    const BlockDiag& b = g.bd;
+    const double coarse = 4.0 * (double)(2 * t.Nc) * (double)(2 * t.Nc);
+    const double transfers = 4.0 * (double)t.interp.n;
+    const double pores = (f32 ? 4.0 : 8.0) * (double)(b.elem_off.empty() ? 0 : b.elem_off.back());
+    const int pb = g.prof.begin(kProfBdApply, coarse + transfers + pores + 32.0 * (double)g.N, g.stream);
     twogrid_apply(g, v, z, done, f32);
     g.prof.end(pb, g.stream);
   } else {

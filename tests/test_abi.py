@@ -42,3 +42,14 @@ def test_null_handle_is_rejected_without_gpu(lib):
     assert lib.lib.stokes_precond_setup(None, 1) == lib.STOKES_EINVAL
     assert "null handle" in lib.stokes_last_error()
     assert lib.lib.stokes_geometry_destroy(None) == lib.STOKES_OK
+
+
+def test_noalloc_binding_checks_array_lengths_without_gpu(lib):
+    """The binding rejects offsets or centres that do not match n_comp
+    before the library would read past their ends."""
+    import numpy as np
+    z = np.zeros(16)
+    with pytest.raises(ValueError):
+        lib.stokes_matvec_noalloc(z, z, z, z, np.array([0, 8], dtype=np.int64), 2, 0, np.zeros(4), z, z)
+    with pytest.raises(ValueError):
+        lib.stokes_matvec_noalloc(z, z, z, z, np.array([0, 8, 16], dtype=np.int64), 2, 0, np.zeros(2), z, z)

@@ -63,6 +63,22 @@ def case(request):
     return request.param, GEOMS[request.param]()
 
 
+def test_newton_reciprocal_matches_ieee_division(S, dev):
+    """The FP64 pair kernel's reciprocal (hardware approximation + two
+    Newton steps) against IEEE division over the squared distances the
+    operator meets (1e-12 .. 1e6, log-uniform), powers of two and the
+    padding sources' 1e60: within 2 ulps."""
+    rng = np.random.default_rng(0)
+    x = np.concatenate([10.0 ** rng.uniform(-12, 6, 200000), 2.0 ** np.arange(-60, 61), [1.0, 3.0, 0.1, 1e60]])
+    xt = torch.tensor(x, device=dev)
+    y = torch.empty_like(xt)
+    S.stokes_rcp_f64(xt, y)
+    torch.cuda.synchronize()
+    ref = 1.0 / x
+    err = np.abs(y.cpu().numpy() - ref) / ref
+    assert err.max() <= 2 * 2.0 ** -53, err.max()
+
+
 def test_matvec_fp64_matches_oracle(S, dev, case):
     name, g = case
     sig = si.random_density(g, 3).reshape(-1)
