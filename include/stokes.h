@@ -78,10 +78,17 @@ enum stokes_precision {
   STOKES_MIXED_IR = 3
 };
 
-enum stokes_pc_kind { STOKES_PC_NONE = 0, STOKES_PC_BLOCKDIAG = 1, STOKES_PC_TWOGRID = 2 };
+enum stokes_pc_kind {
+  STOKES_PC_NONE = 0,
+  STOKES_PC_BLOCKDIAG = 1,
+  STOKES_PC_TWOGRID = 2,     /* set up by stokes_precond_setup_twogrid* */
+  STOKES_PC_BD_LEARNED = 3,  /* block diagonal + learned coarse correction */
+  STOKES_PC_BD_COARSE = 4    /* block diagonal + exact Galerkin coarse correction */
+};
 enum stokes_pc_side { STOKES_PC_RIGHT = 0, STOKES_PC_LEFT = 1 };
 
 typedef struct stokes_geom stokes_geom;
+typedef struct stokes_coarse_model stokes_coarse_model;
 
 /* Build a handle from the discrete boundary (Sec. 2.2: nodes are the
  * collocation points, weights the arclength quadrature weights).
@@ -120,10 +127,26 @@ int stokes_matvec(stokes_geom* g, const double* sigma, double* y, int precision)
  * one block per component, the restriction of A to that component
  * (including its own completion or wall term), assembled on the GPU,
  * LU-factorised with partial pivoting in FP64 and inverted exactly.
- *   pc_kind: STOKES_PC_NONE (drops any existing factors) or STOKES_PC_BLOCKDIAG.
- * Errors: STOKES_EINVAL, STOKES_ENOMEM, STOKES_ECUDA; a singular block
- * (zero pivot) gives STOKES_EBREAKDOWN. */
-int stokes_precond_setup(stokes_geom* g, int pc_kind);
+ *   pc_kind: STOKES_PC_NONE (drops any existing factors),
+ *     STOKES_PC_BLOCKDIAG, or the block diagonal with a second, coarse
+ *     level (the paper has no counterpart; see the coarse-model calls
+ *     below): STOKES_PC_BD_COARSE (exact Galerkin coarse inverse) or
+ *     STOKES_PC_BD_LEARNED (coarse inverse predicted by `model`).
+ *   model: a trained or loaded coarse model for STOKES_PC_BD_LEARNED,
+ *     otherwise ignored (may be NULL).
+ * The coarse level: Z (2N x 3M) holds the rigid motions of each pore p on
+ * its nodes (e_x, e_y and (x - c_p)^perp / r_p, (a, b)^perp = (b, -a),
+ * r_p = L_p / 2 pi with L_p the sum of the pore's weights), W = diag(w),
+ * Y = A Z is formed at setup and with a coarse inverse C each apply is
+ *   c = C Z^T W r,  z = Z c + B^-1 (r - Y c)
+ * (no extra operator application). Exact: C = E^-1, E = Z^T W Y, inverted
+ * by Gauss-Jordan elimination with partial pivoting in FP64 (at most 1365
+ * pores). Learned: C holds only the blocks C[p][q] of q = p and the 16
+ * pores nearest to p. Memory of the coarse level: 16 N M + 72 M^2 bytes.
+ * Errors: STOKES_EINVAL, STOKES_ENOMEM, STOKES_ECUDA; a singular block or
+ * coarse operator gives STOKES_EBREAKDOWN; STOKES_ESTATE for a model that
+ * was never trained or loaded. */
+int stokes_precond_setup(stokes_geom* g, int pc_kind, const stokes_coarse_model* model);
 
 /* Two-grid preconditioner (the paper has no counterpart: a GPU-native
  * alternative to its block-diagonal baseline for densely packed pores):
@@ -383,6 +406,78 @@ int stokes_batch_matvec(stokes_geom* const* geoms, int n_geoms, int n_rhs, const
 int stokes_batch_solve(stokes_geom* const* geoms, int n_geoms, int n_rhs, const double* const* f, double tol,
                        int restart, int max_iter, int precision, double* const* sigma, int* iters,
                        double* relres, int* status);
+
+/* ---- Learned coarse correction (the paper has no counterpart) ----
+ *
+ * A network predicts the coarse level's inverse C (see stokes_precond_setup)
+ * pore by pore: for pore p, the 3 x 3 blocks C[p][q] for q = p and its 16
+ * nearest pores (by centre distance, nearest first, ties to the smaller pore
+ * number), in the scaled form L_p L_q C[p][q], from 35 features:
+ *   x = [c_x / a, c_y / b, r_p, (c_q - c_p) for the 16 nearest q (zeros where
+ *        fewer pores exist)],  a, b = half the wall's extent in x and y.
+ * Output o = 9 j + 3 al + be is entry (al, be) of block j (j = 0: q = p).
+ * Network: y = relu(relu(x W1 + b1) W2 + b2) W3 + b3, 35 -> 256 -> 256 -> 153,
+ * bfloat16 weights and activations on the tensor cores with float
+ * accumulation; float master parameters updated by Adam (b1 = 0.9,
+ * b2 = 0.999, eps = 1e-8). Parameters: a flat float array W1 [35 x 256], b1,
+ * W2 [256 x 256], b2, W3 [256 x 153], b3, matrices row-major.
+ * Training: each stokes_coarse_model_add_geometry call computes, on the
+ * GPU, the geometry's exact E^-1 (as STOKES_PC_BD_COARSE does) and appends
+ * one sample per pore (features, scaled target blocks, a mask of present
+ * blocks); stokes_coarse_model_train standardises features and targets with
+ * the training set's column means and spreads (population; spreads below
+ * 1e-12 count as 1) and takes full-batch Adam steps on the masked mean
+ * squared error. Arrays may be host or device memory unless stated; calls
+ * synchronise the model's stream. */
+
+/* Number of network parameters (114,329). */
+int64_t stokes_coarse_model_num_params(void);
+
+/* A model with initial parameters `params` (n_params floats; the caller
+ * draws them) and zero Adam moments; its GPU work runs on `stream`.
+ * Errors: STOKES_EINVAL, STOKES_ENOMEM, STOKES_ECUDA. */
+int stokes_coarse_model_create(const float* params, int64_t n_params, void* stream, stokes_coarse_model** out);
+int stokes_coarse_model_destroy(stokes_coarse_model* model);
+
+/* Append the training samples of a geometry (one per pore; its coarse
+ * level is computed on the handle's stream and then dropped). */
+int stokes_coarse_model_add_geometry(stokes_coarse_model* model, stokes_geom* g);
+/* Number of training samples (-1 for NULL). */
+int64_t stokes_coarse_model_num_samples(const stokes_coarse_model* model);
+
+/* `steps` full-batch Adam steps with learning rate lr (> 0); *loss_out
+ * (may be NULL) receives the loss of the last step's forward pass.
+ * STOKES_ESTATE without samples. */
+int stokes_coarse_model_train(stokes_coarse_model* model, int steps, double lr, double* loss_out);
+
+/* Parameters (n_params floats) and standardisation (2 * 35 + 2 * 153
+ * floats: feature means, feature spreads, target means, target spreads;
+ * may be NULL when saving) out of / into a model (the caller stores them). */
+int stokes_coarse_model_save(const stokes_coarse_model* model, float* params, float* stats);
+int stokes_coarse_model_load(stokes_coarse_model* model, const float* params, const float* stats);
+
+/* The raw network (no standardisation): y [rows x 153] = net(x [rows x 35]). */
+int stokes_coarse_model_forward(stokes_coarse_model* model, const float* x, int64_t rows, float* y);
+
+/* Masked mean squared error L = sum mask (net(x) - t)^2 / sum mask of the
+ * raw network and its gradient with respect to the flat parameters
+ * (backpropagation through the bfloat16 activations; the output and hidden
+ * gradients are rounded to bfloat16 before each product).
+ *   x [rows x 35], t, mask [rows x 153]; loss: one double (may be NULL);
+ *   grad: n_params floats. */
+int stokes_coarse_model_loss_grad(stokes_coarse_model* model, const float* x, const float* t, const float* mask,
+                                  int64_t rows, double* loss, float* grad);
+
+/* One Adam step of the parameters with the given gradient (n_params floats). */
+int stokes_coarse_model_adam_step(stokes_coarse_model* model, const float* grad, double lr);
+
+/* The coarse-level inputs of a geometry, for checking: features x [M x 35]
+ * and neighbour pore numbers nbr [M x 16] (-1 where absent) of its M pores
+ * in component order; Y = A Z (2N x 3M, column-major) and E = Z^T W Y
+ * (3M x 3M, row-major); outputs may be NULL (stokes_coarse_operator) and
+ * host or device memory. Errors: STOKES_EINVAL (no pore, more than 1365). */
+int stokes_coarse_features(stokes_geom* g, float* x, int* nbr);
+int stokes_coarse_operator(stokes_geom* g, double* y, double* e);
 
 /* Number of library kernels that have started on the current device since
  * the library was loaded (each kernel counts itself once when it begins;

@@ -14,8 +14,10 @@ What it computes:
   the density. The coarse space Z (2N x 3M) holds, for each pore k, the
   three rigid-motion densities on its nodes: e_x, e_y and the rotation
   (x - c_k)^perp / r_k, with (a, b)^perp = (b, -a) as in Sec. 4.2 (zero on
-  every other component). With W = diag(w) on both vector components,
-  Z^T W sigma gives lambda_k and xi_k / r_k.
+  every other component) and r_k = L_k / (2 pi), L_k the sum of the pore's
+  quadrature weights (its perimeter; the radius for a circle). With
+  W = diag(w) on both vector components, Z^T W sigma gives lambda_k and
+  xi_k / r_k.
 * Galerkin coarse operator E = Z^T W A Z (3M x 3M), A the dense operator of
   Eq. 6 (``stokes_oracle.assemble``).
 * Two-level preconditioner (coarse level first, then the block diagonal of
@@ -29,8 +31,10 @@ What it computes:
   half-extents (2), radius of k (1), offsets c_l - c_k of the 16 nearest
   pores (32)]. Network: 35 -> 256 -> 256 -> 153, ReLU after the first two
   layers, weights rounded to bfloat16; the training target is E^-1 on the
-  pattern, standardised per output, and the loss the masked mean squared
-  error. The optimiser is Adam (Kingma and Ba 2015).
+  pattern in the scaled form L_k L_l E^-1[k, l] (perimeter-weighted, so the
+  targets of small and large pores are alike), standardised per output, and
+  the loss the masked mean squared error. The optimiser is Adam (Kingma and
+  Ba 2015).
 """
 from __future__ import annotations
 
@@ -52,16 +56,22 @@ def pore_ids(geom):
     return [k for k in range(geom.n_comp) if k != geom.outer_comp]
 
 
+def perimeters(geom):
+    """L_k = sum of the quadrature weights of each pore (pore order)."""
+    return np.array([geom.weights[geom.comp_slice(k)].sum() for k in pore_ids(geom)])
+
+
 def rigid_modes(geom):
     """Z (2N x 3M): columns 3p, 3p+1, 3p+2 of the p-th pore are e_x, e_y and
-    (x - c)^perp / r on its nodes."""
+    (x - c)^perp / r on its nodes, r = L / (2 pi)."""
     pores = pore_ids(geom)
+    L = perimeters(geom)
     Z = np.zeros((2 * geom.n_nodes, 3 * len(pores)))
     for p, k in enumerate(pores):
         sl = geom.comp_slice(k)
         idx = np.arange(sl.start, sl.stop)
         d = geom.nodes[sl] - geom.centres[k][None, :]
-        r = geom.radii[k]
+        r = L[p] / (2.0 * np.pi)
         Z[2 * idx, 3 * p] = 1.0
         Z[2 * idx + 1, 3 * p + 1] = 1.0
         Z[2 * idx, 3 * p + 2] = d[:, 1] / r
@@ -130,7 +140,7 @@ def pore_features(geom, k=K_NBRS):
     F = np.zeros((len(pores), 3 + 2 * k))
     F[:, 0] = c[:, 0] / a
     F[:, 1] = c[:, 1] / b
-    F[:, 2] = geom.radii[pores]
+    F[:, 2] = perimeters(geom) / (2.0 * np.pi)
     for p in range(len(pores)):
         for j in range(k):
             q = nb[p, j]
@@ -140,11 +150,12 @@ def pore_features(geom, k=K_NBRS):
 
 
 def coarse_targets(geom, Einv=None, k=K_NBRS):
-    """Blocks of E^-1 on the pattern: T (M, 9 (k + 1)) with block j (j = 0:
-    the pore itself, j >= 1: its j-th nearest pore) flattened row-major, and
-    the mask (M, 9 (k + 1)) of present blocks."""
+    """Scaled blocks L_p L_q E^-1[p, q] on the pattern: T (M, 9 (k + 1)) with
+    block j (j = 0: the pore itself, j >= 1: its j-th nearest pore q)
+    flattened row-major, and the mask (M, 9 (k + 1)) of present blocks."""
     if Einv is None:
         Einv = np.linalg.inv(coarse_operator(geom))
+    L = perimeters(geom)
     nb = nearest_neighbours(geom, k)
     M = nb.shape[0]
     T = np.zeros((M, 9 * (k + 1)))
@@ -154,21 +165,22 @@ def coarse_targets(geom, Einv=None, k=K_NBRS):
         for j, q in enumerate(cols):
             if q < 0:
                 continue
-            T[p, 9 * j:9 * j + 9] = Einv[3 * p:3 * p + 3, 3 * q:3 * q + 3].reshape(-1)
+            T[p, 9 * j:9 * j + 9] = L[p] * L[q] * Einv[3 * p:3 * p + 3, 3 * q:3 * q + 3].reshape(-1)
             mask[p, 9 * j:9 * j + 9] = 1.0
     return T, mask
 
 
 def assemble_sparse_inverse(geom, Y, k=K_NBRS):
-    """The dense 3M x 3M matrix C with the predicted blocks Y (M, 9 (k + 1))
-    at the pattern's positions and zeros elsewhere."""
+    """The dense 3M x 3M matrix C with the scaled blocks Y (M, 9 (k + 1))
+    unscaled (divided by L_p L_q) at the pattern's positions, zeros elsewhere."""
+    L = perimeters(geom)
     nb = nearest_neighbours(geom, k)
     M = nb.shape[0]
     C = np.zeros((3 * M, 3 * M))
     for p in range(M):
         for j, q in enumerate([p] + list(nb[p])):
             if q >= 0:
-                C[3 * p:3 * p + 3, 3 * q:3 * q + 3] = Y[p, 9 * j:9 * j + 9].reshape(3, 3)
+                C[3 * p:3 * p + 3, 3 * q:3 * q + 3] = Y[p, 9 * j:9 * j + 9].reshape(3, 3) / (L[p] * L[q])
     return C
 
 

@@ -29,13 +29,18 @@ __all__ = [
     "stokes_pair_shape_count", "stokes_pair_shape_info", "stokes_set_pair_shape", "stokes_get_pair_shape",
     "stokes_autotune", "stokes_tune_cache_insert", "stokes_tune_cache_lookup", "stokes_tune_cache_clear",
     "stokes_tune_cache_save", "stokes_tune_cache_load", "stokes_batch_matvec", "stokes_batch_solve",
-    "stokes_precond_setup_twogrid_ex", "stokes_rcp_f64", "STOKES_TG_COARSE_AUTO", "STOKES_TG_COARSE_INVERSE", "STOKES_TG_COARSE_LU",
+    "stokes_precond_setup_twogrid_ex", "stokes_rcp_f64", "STOKES_PC_BD_LEARNED", "STOKES_PC_BD_COARSE",
+    "stokes_coarse_model_num_params", "stokes_coarse_model_create", "stokes_coarse_model_destroy",
+    "stokes_coarse_model_add_geometry", "stokes_coarse_model_num_samples", "stokes_coarse_model_train",
+    "stokes_coarse_model_save", "stokes_coarse_model_load", "stokes_coarse_model_forward",
+    "stokes_coarse_model_loss_grad", "stokes_coarse_model_adam_step", "stokes_coarse_features",
+    "stokes_coarse_operator", "STOKES_TG_COARSE_AUTO", "STOKES_TG_COARSE_INVERSE", "STOKES_TG_COARSE_LU",
 ]
 
 STOKES_OK, STOKES_EINVAL, STOKES_ENOMEM, STOKES_ECUDA = 0, -1, -2, -3
 STOKES_ENOTCONV, STOKES_EBREAKDOWN, STOKES_ESTATE = -4, -5, -6
 STOKES_FP64, STOKES_FP32, STOKES_DF64, STOKES_MIXED_IR = 0, 1, 2, 3
-STOKES_PC_NONE, STOKES_PC_BLOCKDIAG, STOKES_PC_TWOGRID = 0, 1, 2
+STOKES_PC_NONE, STOKES_PC_BLOCKDIAG, STOKES_PC_TWOGRID, STOKES_PC_BD_LEARNED, STOKES_PC_BD_COARSE = 0, 1, 2, 3, 4
 STOKES_PC_RIGHT, STOKES_PC_LEFT = 0, 1
 STOKES_TG_COARSE_AUTO, STOKES_TG_COARSE_INVERSE, STOKES_TG_COARSE_LU = 0, 1, 2
 (STOKES_PROF_PAIRS_FP64, STOKES_PROF_PAIRS_FP32, STOKES_PROF_PAIRS_DF64, STOKES_PROF_EPILOGUE,
@@ -62,7 +67,20 @@ def _load():
         "stokes_geometry_destroy": (I, [P]),
         "stokes_geometry_num_nodes": (I64, [P]),
         "stokes_matvec": (I, [P, P, P, I]),
-        "stokes_precond_setup": (I, [P, I]),
+        "stokes_precond_setup": (I, [P, I, P]),
+        "stokes_coarse_model_num_params": (I64, []),
+        "stokes_coarse_model_create": (I, [P, I64, P, ctypes.POINTER(P)]),
+        "stokes_coarse_model_destroy": (I, [P]),
+        "stokes_coarse_model_add_geometry": (I, [P, P]),
+        "stokes_coarse_model_num_samples": (I64, [P]),
+        "stokes_coarse_model_train": (I, [P, I, D, ctypes.POINTER(D)]),
+        "stokes_coarse_model_save": (I, [P, P, P]),
+        "stokes_coarse_model_load": (I, [P, P, P]),
+        "stokes_coarse_model_forward": (I, [P, P, I64, P]),
+        "stokes_coarse_model_loss_grad": (I, [P, P, P, P, I64, ctypes.POINTER(D), P]),
+        "stokes_coarse_model_adam_step": (I, [P, P, D]),
+        "stokes_coarse_features": (I, [P, P, P]),
+        "stokes_coarse_operator": (I, [P, P, P]),
         "stokes_precond_setup_twogrid": (I, [P, I]),
         "stokes_precond_setup_twogrid_ex": (I, [P, I, I]),
         "stokes_precond_apply": (I, [P, P, P]),
@@ -156,8 +174,9 @@ def stokes_matvec(handle, sigma, y, precision=STOKES_FP64):
     _check(lib.stokes_matvec(ctypes.c_void_p(handle), _ptr(sigma, count=n2), _ptr(y, count=n2), int(precision)))
 
 
-def stokes_precond_setup(handle, pc_kind=STOKES_PC_BLOCKDIAG):
-    _check(lib.stokes_precond_setup(ctypes.c_void_p(handle), int(pc_kind)))
+def stokes_precond_setup(handle, pc_kind=STOKES_PC_BLOCKDIAG, model=None):
+    _check(lib.stokes_precond_setup(ctypes.c_void_p(handle), int(pc_kind),
+                                    None if model is None else ctypes.c_void_p(model)))
 
 
 def stokes_precond_setup_twogrid(handle, coarsen=8):
@@ -336,6 +355,105 @@ def stokes_batch_solve(handles, n_rhs, f, sigma, tol=1e-8, restart=50, max_iter=
     _check(lib.stokes_batch_solve(_ptr_array(handles), len(handles), int(n_rhs), _ptr_array(f, ns), float(tol),
                                   int(restart), int(max_iter), int(precision), _ptr_array(sigma, ns), it, rr, st))
     return list(it), list(rr), list(st)
+
+
+def _fptr(a, count):
+    """Address of a C-contiguous float32 (or int32) numpy array or torch tensor."""
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous() or a.element_size() != 4 or a.numel() != count:
+            raise TypeError(f"expected a contiguous 4-byte tensor of {count} elements")
+        return ctypes.c_void_p(a.data_ptr())
+    if not isinstance(a, np.ndarray) or a.dtype not in (np.float32, np.int32) or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("expected a C-contiguous float32 or int32 array")
+    if a.size != count:
+        raise ValueError(f"expected {count} elements, got {a.size}")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+COARSE_FEATURES, COARSE_OUTPUTS, COARSE_NEIGHBOURS = 35, 153, 16
+COARSE_STATS = 2 * COARSE_FEATURES + 2 * COARSE_OUTPUTS
+
+
+def stokes_coarse_model_num_params() -> int:
+    return int(lib.stokes_coarse_model_num_params())
+
+
+def stokes_coarse_model_create(params, stream=None):
+    """A coarse model from initial float32 parameters; returns its handle."""
+    n = stokes_coarse_model_num_params()
+    h = ctypes.c_void_p()
+    st = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(lib.stokes_coarse_model_create(_fptr(params, n), ctypes.c_int64(n), st, ctypes.byref(h)))
+    return h.value
+
+
+def stokes_coarse_model_destroy(model):
+    _check(lib.stokes_coarse_model_destroy(ctypes.c_void_p(model)))
+
+
+def stokes_coarse_model_add_geometry(model, handle):
+    _check(lib.stokes_coarse_model_add_geometry(ctypes.c_void_p(model), ctypes.c_void_p(handle)))
+
+
+def stokes_coarse_model_num_samples(model) -> int:
+    return int(lib.stokes_coarse_model_num_samples(ctypes.c_void_p(model)))
+
+
+def stokes_coarse_model_train(model, steps, lr):
+    """Returns the loss of the last step."""
+    loss = ctypes.c_double(0.0)
+    _check(lib.stokes_coarse_model_train(ctypes.c_void_p(model), int(steps), float(lr), ctypes.byref(loss)))
+    return loss.value
+
+
+def stokes_coarse_model_save(model, params, stats=None):
+    _check(lib.stokes_coarse_model_save(ctypes.c_void_p(model), _fptr(params, stokes_coarse_model_num_params()),
+                                        None if stats is None else _fptr(stats, COARSE_STATS)))
+
+
+def stokes_coarse_model_load(model, params, stats):
+    _check(lib.stokes_coarse_model_load(ctypes.c_void_p(model), _fptr(params, stokes_coarse_model_num_params()),
+                                        _fptr(stats, COARSE_STATS)))
+
+
+def stokes_coarse_model_forward(model, x, y):
+    rows = (x.numel() if hasattr(x, "numel") else x.size) // COARSE_FEATURES
+    _check(lib.stokes_coarse_model_forward(ctypes.c_void_p(model), _fptr(x, rows * COARSE_FEATURES),
+                                           ctypes.c_int64(rows), _fptr(y, rows * COARSE_OUTPUTS)))
+
+
+def stokes_coarse_model_loss_grad(model, x, t, mask, grad):
+    """Returns the loss; the gradient is written into `grad`."""
+    rows = (x.numel() if hasattr(x, "numel") else x.size) // COARSE_FEATURES
+    loss = ctypes.c_double(0.0)
+    _check(lib.stokes_coarse_model_loss_grad(ctypes.c_void_p(model), _fptr(x, rows * COARSE_FEATURES),
+                                             _fptr(t, rows * COARSE_OUTPUTS), _fptr(mask, rows * COARSE_OUTPUTS),
+                                             ctypes.c_int64(rows), ctypes.byref(loss),
+                                             _fptr(grad, stokes_coarse_model_num_params())))
+    return loss.value
+
+
+def stokes_coarse_model_adam_step(model, grad, lr):
+    _check(lib.stokes_coarse_model_adam_step(ctypes.c_void_p(model), _fptr(grad, stokes_coarse_model_num_params()),
+                                             float(lr)))
+
+
+def stokes_coarse_features(handle, n_pores):
+    """Returns (features float32 [M x 35], neighbours int32 [M x 16])."""
+    x = np.zeros((n_pores, COARSE_FEATURES), dtype=np.float32)
+    nb = np.zeros((n_pores, COARSE_NEIGHBOURS), dtype=np.int32)
+    _check(lib.stokes_coarse_features(ctypes.c_void_p(handle), _fptr(x, x.size), _fptr(nb, nb.size)))
+    return x, nb
+
+
+def stokes_coarse_operator(handle, n_pores):
+    """Returns (Y = A Z [2N x 3M], E = Z^T W Y [3M x 3M]) as float64 arrays."""
+    n2 = 2 * stokes_geometry_num_nodes(handle)
+    m = 3 * n_pores
+    y = np.zeros(n2 * m)
+    e = np.zeros(m * m)
+    _check(lib.stokes_coarse_operator(ctypes.c_void_p(handle), _ptr(y, count=n2 * m), _ptr(e, count=m * m)))
+    return y.reshape(m, n2).T, e.reshape(m, m)
 
 
 def stokes_rcp_f64(x, y, stream=None):

@@ -120,23 +120,6 @@ int stokes_matvec(stokes_geom* h, const double* sigma, double* y, int precision)
   });
 }
 
-int stokes_precond_setup(stokes_geom* h, int pc_kind) {
-  return guarded([&] {
-    Geom& g = handle(h);
-    stokes::require(pc_kind == STOKES_PC_NONE || pc_kind == STOKES_PC_BLOCKDIAG, "unknown pc_kind");
-    g.tg.ready = false;
-    g.bd.ready = false;
-    if (pc_kind == STOKES_PC_NONE) {
-      g.bd.lu.release();
-      g.bd.inv.release();
-      g.tg.lu.release();
-      return;
-    }
-    g.tg.lu.release();
-    stokes::bd_setup(g);
-  });
-}
-
 int stokes_precond_setup_twogrid(stokes_geom* h, int coarsen) {
   return stokes_precond_setup_twogrid_ex(h, coarsen, STOKES_TG_COARSE_AUTO);
 }
@@ -149,6 +132,7 @@ int stokes_precond_setup_twogrid_ex(stokes_geom* h, int coarsen, int coarse_mode
                     "unknown coarse_mode");
     g.tg.ready = false;
     g.bd.ready = false;
+    g.cl.ready = false;
     stokes::twogrid_setup(g, coarsen, coarse_mode);
   });
 }
@@ -265,7 +249,8 @@ int64_t stokes_kernel_launches(void) {
   try {
     return (int64_t)(stokes::launches_geometry() + stokes::launches_dlp_f64() + stokes::launches_dlp_f32() +
                      stokes::launches_dlp_df64() + stokes::launches_bd() + stokes::launches_bd_trsv() + stokes::launches_bd_inv32() + stokes::launches_twogrid() +
-                     stokes::launches_gmres() + stokes::launches_batch() + stokes::launches_noalloc());
+                     stokes::launches_gmres() + stokes::launches_batch() + stokes::launches_noalloc() +
+                     stokes::launches_mlp() + stokes::launches_coarse() + stokes::launches_tc_gemm());
   } catch (...) {
     return -1;
   }

@@ -589,8 +589,17 @@ static void bd_setup_impl(Geom& g, bool skip_wall) {
   }
   if (tri_total) {
     b.lu32.alloc(tri_total);
-    b.work32.alloc(tri_max);
-    b.work64.alloc(tri_max);
+    b.work32.alloc(2 * tri_max);
+    b.work64.alloc(2 * tri_max);
+    b.tinv_off.assign(nc, -1);
+    int64_t ti_total = 0;
+    for (int k : b.tri_ids) {
+      b.tinv_off[k] = ti_total;
+      ti_total += lu_tile_inverse_elems(b.rows[k]);
+    }
+    b.tinv64.alloc(ti_total);
+    for (int k : b.tri_ids)
+      lu_tile_inverses<double>(s, b.lu.get() + b.elem_off[k], b.rows[k], b.tinv64.get() + b.tinv_off[k]);
     for (int k : b.tri_ids) {
       const int64_t mm = b.rows[k] * b.rows[k];
       k_to_f32<<<(unsigned)std::min<int64_t>((mm + 255) / 256, 152 * 32), 256, 0, s>>>(
@@ -637,8 +646,8 @@ void bd_apply(Geom& g, const double* v, double* z, const int* done, bool f32) {
     for (int k : b.tri_ids) {
       const int64_t m = b.rows[k];
       const int64_t o = 2 * g.off[k];
-      lu_solve_persistent<double>(g, b.lu.get() + b.elem_off[k], m, b.perm.get() + b.piv_off[k], v + o, z + o,
-                                  b.work64.get(), done);
+      lu_solve_persistent<double>(g, b.lu.get() + b.elem_off[k], m, b.perm.get() + b.piv_off[k],
+                                  b.tinv64.get() + b.tinv_off[k], v + o, z + o, b.work64.get(), done);
     }
   }
   g.prof.end(pb, s);

@@ -1,17 +1,24 @@
 // Triangular solves with the LU factors of the largest preconditioner
 // blocks (too large to invert explicitly), one persistent kernel per solve.
 //
-// z = U^-1 L^-1 P v for a column-major m x m block. The grid is one CTA per
-// SM, launched cooperatively so all CTAs are resident; rows are cut into
-// tiles of kTs and tile u belongs to CTA u mod gridDim.x. Forward sweep,
-// phase t: every CTA subtracts L[u, t] z_t from each of its tiles u > t; the
-// owner of tile t + 1 updates that tile first and then solves its unit
-// lower diagonal block in shared memory; a grid barrier ends the phase.
-// The backward sweep mirrors it from the last tile with U's diagonal.
+// z = U^-1 L^-1 P v for a column-major m x m block (L unit lower below the
+// diagonal, U on and above it). Rows are cut into tiles of kTs; tile u
+// belongs to CTA u mod gridDim.x, which keeps the tile's running right-hand
+// side in shared memory. The inverses of the diagonal tiles are formed once
+// at setup (lu_tile_inverses), so solving a tile is one small product.
+// Forward sweep over t = 0, 1, ...: the owner of tile t publishes x_t
+// (global memory, then a per-tile flag carrying this launch's generation
+// number); every CTA waits for the flag of t, then subtracts L[u, t] x_t from
+// each of its tiles u > t, the owner of t + 1 first, which solves and
+// publishes t + 1 at once: the chain of dependent tile solves is the only
+// serial part, and the other updates stream the factors at the memory's
+// rate behind it. The backward sweep mirrors it with U from the last tile.
 //
-// The grid barrier (grid_sync.cuh) spins with an iteration limit: on
-// timeout it raises an error flag, every CTA leaves at the next check, and
-// the host reports the failure instead of hanging.
+// Every wait on a flag polls with an iteration limit: on timeout the CTA
+// raises the sticky error word, every other CTA sees it at its next poll
+// and leaves, and the host reports the failure instead of hanging. All
+// CTAs are resident (cooperative launch, one CTA per SM), so a flag that
+// will be set is always set by a running CTA.
 #include <algorithm>
 
 #include "grid_sync.cuh"
@@ -22,145 +29,263 @@ namespace {
 
 constexpr int kTs = 64;
 constexpr int kThreads = 256;
-using gsync::Barrier;
-using gsync::grid_sync;
 
+__device__ __forceinline__ unsigned ld_volatile_u32(const unsigned* p) { return *(volatile const unsigned*)p; }
+
+// Wait (thread 0) until flag == gen; false if this or another CTA gave up.
+__device__ __forceinline__ bool wait_flag(const unsigned* flag, unsigned gen, int* err, long long limit) {
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    long long spins = 0;
+    int ok = 1;
+    while (ld_volatile_u32(flag) != gen) {
+      if (++spins > limit || *(volatile int*)err) {
+        atomicExch(err, 1);
+        ok = 0;
+        break;
+      }
+      __nanosleep(20);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// x (forward solutions) and y (backward solutions): m elements each.
 template <class T>
 __global__ void __launch_bounds__(kThreads)
-k_lu_solve_persistent(const T* __restrict__ A, int64_t m, const int* __restrict__ perm,
-                      const double* __restrict__ v, T* __restrict__ z, double* __restrict__ out, Barrier bar,
-                      const int* __restrict__ done) {
+k_lu_solve_flags(const T* __restrict__ A, int64_t m, const int* __restrict__ perm, const T* __restrict__ tinv,
+                 const double* __restrict__ v, T* __restrict__ work, double* __restrict__ out,
+                 unsigned* __restrict__ flags, unsigned gen, int* __restrict__ err, long long limit,
+                 const int* __restrict__ done) {
   count_launch();
   if (done && *done) return;
-  __shared__ T sT[kTs][kTs + 1];  // a diagonal tile, [col][row]
+  extern __shared__ unsigned char smem_raw[];
+  T* acc = reinterpret_cast<T*>(smem_raw);  // [my tiles][kTs]
   __shared__ T sz[kTs];
   __shared__ T red[4][kTs];
   const int64_t nt = (m + kTs - 1) / kTs;
-  const int G = gridDim.x;
-  unsigned epoch = 0;
-  // z = P v
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m; r += (int64_t)G * blockDim.x)
-    z[r] = (T)v[perm[r]];
-  if (!grid_sync(bar, epoch)) return;
+  const int G = gridDim.x, me = blockIdx.x;
+  const int mine = (int)((nt - me + G - 1) / G);  // tiles me, me + G, ...
+  if (mine <= 0) return;                          // nothing to solve or update here
+  const int64_t last = me + (int64_t)(mine - 1) * G;
+  const int rr = threadIdx.x & (kTs - 1), ph = threadIdx.x / kTs;
+  const T* invL = tinv;
+  const T* invU = tinv + nt * kTs * kTs;
+  T* x = work;
+  T* y = work + m;
 
-  // Solve the diagonal tile u in place (lower: unit; upper: divide by the diagonal).
-  auto solve_tile = [&](int64_t u, bool lower) {
-    const int64_t r0 = u * kTs;
-    const int nt_u = (int)imin64(kTs, m - r0);
-    for (int e = threadIdx.x; e < nt_u * nt_u; e += blockDim.x) {
-      const int c = e / nt_u, r = e % nt_u;
-      sT[c][r] = A[(r0 + c) * m + r0 + r];
-    }
-    if (threadIdx.x < nt_u) sz[threadIdx.x] = z[r0 + threadIdx.x];
-    __syncthreads();
-    const int r = threadIdx.x;
-    if (lower) {
-      for (int c = 0; c < nt_u; ++c) {
-        if (r > c && r < nt_u) sz[r] -= sT[c][r] * sz[c];
-        __syncthreads();
-      }
-    } else {
-      for (int c = nt_u - 1; c >= 0; --c) {
-        if (r == c) sz[c] /= sT[c][c];
-        __syncthreads();
-        if (r < c) sz[r] -= sT[c][r] * sz[c];
-        __syncthreads();
-      }
-    }
-    if (r < nt_u) z[r0 + r] = sz[r];
-    __syncthreads();
-  };
+  // acc_u = (P v)_u
+  for (int e = threadIdx.x; e < mine * kTs; e += kThreads) {
+    const int64_t row = (int64_t)(me + (e / kTs) * G) * kTs + (e % kTs);
+    acc[e] = row < m ? (T)v[perm[row]] : (T)0;
+  }
+  __syncthreads();
 
-  // z_u -= A[u rows, t cols] z_t for one tile u (rows of u, columns of t).
-  auto update_tile = [&](int64_t u, int64_t t) {
+  // a -= A[u tile rows, t tile columns] sz
+  auto update = [&](int64_t u, int64_t t, T* a) {
     const int64_t r0 = u * kTs, c0 = t * kTs;
-    const int nr = (int)imin64(kTs, m - r0), nc = (int)imin64(kTs, m - c0);
-    if (threadIdx.x < nc) sz[threadIdx.x] = z[c0 + threadIdx.x];
+    const int nc = (int)imin64(kTs, m - c0);
+    T s = 0;
+    if (r0 + rr < m) {
+      const T* col = A + c0 * m + r0 + rr;
+#pragma unroll 4
+      for (int c = ph; c < nc; c += 4) s += col[(int64_t)c * m] * sz[c];
+    }
+    red[ph][rr] = s;
     __syncthreads();
-    // 256 threads: 64 rows x 4 column phases
-    const int rr = threadIdx.x & (kTs - 1), ph = threadIdx.x / kTs;
-    T acc = 0;
-    if (rr < nr)
-      for (int c = ph; c < nc; c += 4) acc += A[(c0 + c) * m + r0 + rr] * sz[c];
-    red[ph][rr] = acc;
+    if (ph == 0) a[rr] -= (red[0][rr] + red[1][rr]) + (red[2][rr] + red[3][rr]);
     __syncthreads();
-    if (ph == 0 && rr < nr) z[r0 + rr] -= (red[0][rr] + red[1][rr]) + (red[2][rr] + red[3][rr]);
+  };
+  // a = inv(T_tt) a (column-major tile inverse), also written to dst (global)
+  auto solve = [&](int64_t t, const T* inv, T* a, T* dst) {
+    const T* X = inv + t * kTs * kTs;
+    T s = 0;
+#pragma unroll 4
+    for (int c = ph; c < kTs; c += 4) s += X[c * kTs + rr] * a[c];
+    red[ph][rr] = s;
+    __syncthreads();
+    if (ph == 0) {
+      const T val = (red[0][rr] + red[1][rr]) + (red[2][rr] + red[3][rr]);
+      a[rr] = val;
+      if (t * kTs + rr < m) {
+        dst[t * kTs + rr] = val;
+        __threadfence();
+      }
+    }
+    __syncthreads();
+  };
+  auto publish = [&](unsigned* f) {
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicExch(f, gen);
+    }
+  };
+  // sz = the solution of tile t: this CTA's own copy, or the published one
+  auto fetch = [&](int64_t t, const T* src) {
+    if (threadIdx.x < kTs) {
+      if (t % G == me) sz[threadIdx.x] = acc[(t / G) * kTs + threadIdx.x];
+      else sz[threadIdx.x] = t * kTs + threadIdx.x < m ? __ldcg(src + t * kTs + threadIdx.x) : (T)0;
+    }
     __syncthreads();
   };
 
-  // forward sweep (unit lower L)
-  if (blockIdx.x == 0) solve_tile(0, true);
-  if (!grid_sync(bar, epoch)) return;
-  for (int64_t t = 0; t + 1 < nt; ++t) {
-    const int64_t first = t + 1;
-    // this CTA's tiles u > t: u = first + ((blockIdx.x - first) mod G) + k G
-    int64_t u0 = first + (((int64_t)blockIdx.x - first) % G + G) % G;
-    for (int64_t u = u0; u < nt; u += G) {
-      update_tile(u, t);
-      if (u == first) solve_tile(u, true);
-    }
-    if (!grid_sync(bar, epoch)) return;
+  // forward sweep: L (unit lower)
+  if (me == 0) {
+    solve(0, invL, acc, x);
+    publish(flags);
   }
-  // backward sweep (upper U)
-  if ((nt - 1) % G == blockIdx.x) solve_tile(nt - 1, false);
-  if (!grid_sync(bar, epoch)) return;
-  for (int64_t t = nt - 1; t > 0; --t) {
-    const int64_t first = t - 1;
-    // this CTA's tiles u < t, the one nearest the diagonal first
-    int64_t u0 = first - ((first - (int64_t)blockIdx.x) % G + G) % G;
-    for (int64_t u = u0; u >= 0; u -= G) {
-      update_tile(u, t);
-      if (u == first) solve_tile(u, false);
+  for (int64_t t = 0; t < last; ++t) {  // beyond `last` this CTA has no tile to update
+    if (t % G != me && !wait_flag(flags + t, gen, err, limit)) return;
+    fetch(t, x);
+    const int64_t nxt = t + 1;
+    int64_t u = nxt + ((me - nxt) % G + G) % G;  // this CTA's first tile after t
+    if (u == nxt) {  // it gates the next step: update, solve and publish it first
+      T* a = acc + (nxt / G) * kTs;
+      update(nxt, t, a);
+      solve(nxt, invL, a, x);
+      publish(flags + nxt);
+      u += G;
     }
-    if (!grid_sync(bar, epoch)) return;
+    for (; u < nt; u += G) update(u, t, acc + (u / G) * kTs);
   }
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m; r += (int64_t)G * blockDim.x)
-    out[r] = (double)z[r];
+
+  // backward sweep: U (upper, with its diagonal) from the forward solution in acc
+  unsigned* bflags = flags + nt;
+  if (last == nt - 1) {
+    solve(nt - 1, invU, acc + ((nt - 1) / G) * kTs, y);
+    publish(bflags + nt - 1);
+  }
+  for (int64_t t = nt - 1; t > me; --t) {  // at or below `me` this CTA has no tile to update
+    if (t % G != me && !wait_flag(bflags + t, gen, err, limit)) return;
+    fetch(t, y);
+    const int64_t prv = t - 1;
+    int64_t u = prv - ((prv - me) % G + G) % G;  // this CTA's last tile before t
+    if (u == prv) {
+      T* a = acc + (prv / G) * kTs;
+      update(prv, t, a);
+      solve(prv, invU, a, y);
+      publish(bflags + prv);
+      u -= G;
+    }
+    for (; u >= 0; u -= G) update(u, t, acc + (u / G) * kTs);
+  }
+  for (int e = threadIdx.x; e < mine * kTs; e += kThreads) {
+    const int64_t row = (int64_t)(me + (e / kTs) * G) * kTs + (e % kTs);
+    if (row < m) out[row] = (double)acc[e];
+  }
+}
+
+// Inverse of each diagonal tile of L (unit lower; lower = 1) or U (upper),
+// kTs x kTs, column-major into out[t * kTs * kTs]; a partial last tile is
+// completed with the identity. One CTA per tile; thread q solves for column q.
+template <class T>
+__global__ void __launch_bounds__(kTs)
+k_tile_inverse_t(const T* __restrict__ A, int64_t m, int lower, T* __restrict__ out) {
+  count_launch();
+  const int64_t t = blockIdx.x;
+  const int64_t r0 = t * kTs;
+  const int n = (int)imin64(kTs, m - r0);
+  __shared__ T sT[kTs][kTs + 1];  // [col][row]
+  __shared__ T sX[kTs][kTs + 1];
+  for (int e = threadIdx.x; e < kTs * kTs; e += blockDim.x) {
+    const int c = e / kTs, r = e % kTs;
+    sT[c][r] = (c < n && r < n) ? A[(r0 + c) * m + r0 + r] : (c == r ? (T)1 : (T)0);
+    sX[c][r] = c == r ? (T)1 : (T)0;
+  }
+  __syncthreads();
+  const int q = threadIdx.x;
+  if (lower) {
+    for (int c = 0; c < kTs; ++c) {
+      const T xc = sX[q][c];
+      for (int r = c + 1; r < kTs; ++r) sX[q][r] -= sT[c][r] * xc;
+    }
+  } else {
+    for (int c = kTs - 1; c >= 0; --c) {
+      const T xc = sX[q][c] / sT[c][c];
+      sX[q][c] = xc;
+      for (int r = 0; r < c; ++r) sX[q][r] -= sT[c][r] * xc;
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kTs * kTs; e += blockDim.x) {
+    const int c = e / kTs, r = e % kTs;
+    out[t * kTs * kTs + (int64_t)c * kTs + r] = sX[c][r];
+  }
 }
 
 }  // namespace
 
-// z (2N doubles, block rows [o, o + m)) = factors^-1 v for one block.
-// T = double uses the FP64 factors, T = float a float copy of them.
+int64_t lu_tile_inverse_elems(int64_t m) { return 2 * ((m + kTs - 1) / kTs) * kTs * kTs; }
+
+// tinv: lu_tile_inverse_elems(m) elements, the L tile inverses then the U ones.
 template <class T>
-void lu_solve_persistent(Geom& g, const T* A, int64_t m, const int* perm, const double* v, double* z, T* work,
-                         const int* done) {
+void lu_tile_inverses(cudaStream_t s, const T* A, int64_t m, T* tinv) {
+  const int64_t nt = (m + kTs - 1) / kTs;
+  k_tile_inverse_t<T><<<(unsigned)nt, kTs, 0, s>>>(A, m, 1, tinv);
+  k_tile_inverse_t<T><<<(unsigned)nt, kTs, 0, s>>>(A, m, 0, tinv + nt * kTs * kTs);
+  STOKES_LAUNCHED();
+}
+
+// z (block rows) = factors^-1 v for one block. T = double uses the FP64
+// factors, T = float a float copy of them; work: 2 m elements of T.
+template <class T>
+void lu_solve_persistent(Geom& g, const T* A, int64_t m, const int* perm, const T* tinv, const double* v, double* z,
+                         T* work, const int* done) {
   static int grid = 0;
+  const int64_t nt = (m + kTs - 1) / kTs;
+  BlockDiag& b = g.bd;
   if (grid == 0) {
-    int dev = 0, nsm = 0, per_sm = 0;
+    int dev = 0, nsm = 0;
     STOKES_CUDA(cudaGetDevice(&dev));
     STOKES_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    STOKES_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lu_solve_persistent<T>, kThreads, 0));
-    require(per_sm >= 1, "persistent triangular solve does not fit on an SM", STOKES_ECUDA);
     grid = nsm;  // one CTA per SM: all resident
   }
-  BlockDiag& b = g.bd;
+  const size_t smem = (size_t)((nt + grid - 1) / grid) * kTs * sizeof(T);
+  require(smem <= 48 * 1024, "triangular solve: block too large for the per-CTA tile store");
+  int per_sm = 0;
+  STOKES_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lu_solve_flags<T>, kThreads, smem));
+  require(per_sm >= 1, "persistent triangular solve does not fit on an SM", STOKES_ECUDA);
   if (!b.barrier.get()) {
     b.barrier.alloc(4);
     STOKES_CUDA(cudaMemsetAsync(b.barrier.get(), 0, 4 * sizeof(unsigned), g.stream));
   }
-  // count and generation restart at zero; the error word (slot 2) is sticky
-  STOKES_CUDA(cudaMemsetAsync(b.barrier.get(), 0, 2 * sizeof(unsigned), g.stream));
-  Barrier bar{b.barrier.get(), b.barrier.get() + 1, (int*)(b.barrier.get() + 2), gsync::spin_limit()};
-  void* args[] = {(void*)&A, (void*)&m, (void*)&perm, (void*)&v, (void*)&work, (void*)&z, (void*)&bar,
-                  (void*)&done};
-  STOKES_CUDA(cudaLaunchCooperativeKernel((const void*)k_lu_solve_persistent<T>, dim3(grid), dim3(kThreads), args,
-                                          0, g.stream));
+  if (b.trsv_flags.n < (size_t)(2 * nt)) {
+    b.trsv_flags.alloc(2 * nt);
+    STOKES_CUDA(cudaMemsetAsync(b.trsv_flags.get(), 0, 2 * nt * sizeof(unsigned), g.stream));
+    b.trsv_gen = 0;
+  }
+  unsigned gen = ++b.trsv_gen;
+  if (gen == 0) {  // wrapped: clear the flags so that no stale generation matches
+    STOKES_CUDA(cudaMemsetAsync(b.trsv_flags.get(), 0, b.trsv_flags.n * sizeof(unsigned), g.stream));
+    gen = b.trsv_gen = 1;
+  }
+  unsigned* flags = b.trsv_flags.get();
+  int* err = (int*)(b.barrier.get() + 2);
+  long long limit = gsync::spin_limit();
+  void* args[] = {(void*)&A, (void*)&m, (void*)&perm, (void*)&tinv, (void*)&v, (void*)&work, (void*)&z,
+                  (void*)&flags, (void*)&gen, (void*)&err, (void*)&limit, (void*)&done};
+  STOKES_CUDA(cudaLaunchCooperativeKernel((const void*)k_lu_solve_flags<T>, dim3(grid), dim3(kThreads), args, smem,
+                                          g.stream));
 }
 
-// Throws if a persistent solve's grid barrier ever timed out (synchronises).
+// Throws if a persistent solve ever timed out waiting (synchronises).
 void bd_check_barrier(Geom& g) {
   if (!g.bd.barrier.get()) return;
   unsigned err = 0;
   STOKES_CUDA(cudaMemcpyAsync(&err, g.bd.barrier.get() + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, g.stream));
   STOKES_CUDA(cudaStreamSynchronize(g.stream));
-  require(err == 0, "block-diagonal triangular solve: grid barrier timed out", STOKES_ECUDA);
+  require(err == 0, "block-diagonal triangular solve: a wait for another CTA's tile timed out", STOKES_ECUDA);
 }
 
-template void lu_solve_persistent<double>(Geom&, const double*, int64_t, const int*, const double*, double*,
-                                          double*, const int*);
-template void lu_solve_persistent<float>(Geom&, const float*, int64_t, const int*, const double*, double*, float*,
-                                         const int*);
+template void lu_tile_inverses<double>(cudaStream_t, const double*, int64_t, double*);
+template void lu_tile_inverses<float>(cudaStream_t, const float*, int64_t, float*);
+template void lu_solve_persistent<double>(Geom&, const double*, int64_t, const int*, const double*, const double*,
+                                          double*, double*, const int*);
+template void lu_solve_persistent<float>(Geom&, const float*, int64_t, const int*, const float*, const double*,
+                                         double*, float*, const int*);
 
 unsigned long long launches_bd_trsv() { return tu_launches(); }
 

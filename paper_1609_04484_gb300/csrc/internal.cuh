@@ -101,7 +101,11 @@ struct BlockDiag {
   DevBuf<int> d_tri_ids;          // blocks applied by triangular solves in FP64
   int64_t max_tri_rows = 0;
   DevBuf<double> work64;
+  DevBuf<double> tinv64;          // diagonal-tile inverses of the FP64 triangular-solve blocks
+  std::vector<int64_t> tinv_off;  // per component offset into tinv64 (-1 if none)
   DevBuf<unsigned> barrier;       // count, generation, sticky error
+  DevBuf<unsigned> trsv_flags;    // per-tile ready flags of the persistent triangular solves
+  unsigned trsv_gen = 0;          // generation number of the last such launch
 };
 
 // Workspace of the Krylov solver.
@@ -197,6 +201,7 @@ struct TwoGrid {
   DevBuf<unsigned> barrier;        // grid barrier of the cooperative panel factorisation
   int64_t max_chunks = 0;
   DevBuf<float> work32;
+  DevBuf<float> tinv;              // diagonal-tile inverses of the coarse LU factors
   DevBuf<int> d_pore_ids;
 };
 
@@ -209,6 +214,21 @@ struct PairVariant {
 struct PairShape {
   int variant = -1;     // < 0: not chosen (defaults or the tuner's cache decide)
   int ctas_per_sm = 4;
+};
+
+// Coarse level of the two-level preconditioner (rigid-motion modes of each
+// pore; see coarse.cu).
+struct CoarseLevel {
+  bool ready = false;
+  bool learned = false;
+  int M = 0;                   // pores
+  std::vector<int> pores;      // component of each pore
+  DevBuf<int> d_pores;         // component of pore p
+  DevBuf<int> pore_of;         // pore number of each component (-1 for the wall)
+  DevBuf<double> stats;        // per pore: L = sum w, r = L / 2 pi, sum w dx, sum w dy, sum w |d|^2
+  DevBuf<double> Y;            // A Z, 2N x 3M column-major
+  DevBuf<double> C;            // coarse inverse, 3M x 3M row-major
+  DevBuf<double> rc, c, t;     // Z^T W r, C rc, r - Y c
 };
 
 struct Geom {
@@ -255,6 +275,7 @@ struct Geom {
 
   BlockDiag bd;
   TwoGrid tg;
+  CoarseLevel cl;
   Krylov kr;
   Prof prof;
 };
@@ -271,6 +292,9 @@ unsigned long long launches_twogrid();
 unsigned long long launches_gmres();
 unsigned long long launches_batch();
 unsigned long long launches_noalloc();
+unsigned long long launches_mlp();
+unsigned long long launches_tc_gemm();
+unsigned long long launches_coarse();
 
 // ---- geometry.cu ----
 // component moments (lambda_x, lambda_y, xi, s0) of sigma into `out`
@@ -322,9 +346,27 @@ void invert_from_lu32(Geom& g, const float* LU, int64_t m, const int* perm, floa
 void sgemm32(cudaStream_t s, int64_t M, int64_t N, int K, float alpha, const float* A, int64_t lda, const float* B,
              int64_t ldb, float beta, float* C, int64_t ldc);
 
+// ---- tc_gemm.cu ----
+// false when STOKES_TG_GEMM=simt selects the CUDA-core trailing updates
+bool tc_trailing_enabled();
+// A[b.., b..] -= A[b.., k0..k0+64) A[k0..k0+64), b..), b = k0 + 64 (column-major
+// float m x m) on the tensor cores (three TF32 products); work: tc_trailing_work_floats(m)
+void tc_trailing_update(cudaStream_t s, float* A, int64_t m, int64_t k0, int64_t rest, float* work, int* err);
+int64_t tc_trailing_work_floats(int64_t m);
+
+// ---- bd_trsv.cu ----
+// elements of the diagonal-tile inverses of an m x m LU (L's, then U's)
+int64_t lu_tile_inverse_elems(int64_t m);
 template <class T>
-void lu_solve_persistent(Geom& g, const T* A, int64_t m, const int* perm, const double* v, double* z, T* work,
-                         const int* done);
+void lu_tile_inverses(cudaStream_t s, const T* A, int64_t m, T* tinv);
+// z = U^-1 L^-1 P v by the persistent flag-synchronised solve; work: 2 m elements
+template <class T>
+void lu_solve_persistent(Geom& g, const T* A, int64_t m, const int* perm, const T* tinv, const double* v, double* z,
+                         T* work, const int* done);
+
+// ---- coarse.cu ----
+// z = Z c + B^-1 (r - Y c), c = C Z^T W r (needs cl.ready and the block diagonal)
+void coarse_apply(Geom& g, const double* r, double* z, const int* done, bool f32);
 
 // ---- gmres.cu ----
 struct SolveResult {

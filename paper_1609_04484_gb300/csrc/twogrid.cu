@@ -661,6 +661,12 @@ void twogrid_setup(Geom& g, int q, int coarse_mode) {
   t.barrier.alloc(4);
   STOKES_CUDA(cudaMemsetAsync(t.barrier.get(), 0, 4 * sizeof(unsigned), s));
   float* A = t.lu.get();
+  // trailing updates on the tensor cores (three TF32 products per term)
+  // where the trailing block has at least 256 rows; STOKES_TG_GEMM=simt
+  // keeps the CUDA-core GEMM throughout
+  const bool tc = tc_trailing_enabled();
+  DevBuf<float> tc_work;
+  if (tc && m > 256) tc_work.alloc(tc_trailing_work_floats(m));
   // with STOKES_TRACE: time of the panel factorisations and of the trailing
   // updates, from events around each phase
   std::vector<cudaEvent_t> ev;
@@ -707,7 +713,10 @@ void twogrid_setup(Geom& g, int q, int coarse_mode) {
       // A22 -= L21 U12 (rows and columns from k0 + kb on)
       const int64_t base = k0 + kb;
       const int pg = g.prof.begin(kProfLuGemm, 2.0 * (double)rest * (double)rest * kb, s);
-      sgemm32(s, rest, rest, kb, -1.f, A + k0 * m + base, m, A + base * m + k0, m, 1.f, A + base * m + base, m);
+      if (tc && kb == kNb && rest >= 256)
+        tc_trailing_update(s, A, m, k0, rest, tc_work.get(), (int*)(t.barrier.get() + 2));
+      else
+        sgemm32(s, rest, rest, kb, -1.f, A + k0 * m + base, m, A + base * m + k0, m, 1.f, A + base * m + base, m);
       g.prof.end(pg, s);
     }
     STOKES_LAUNCHED();
@@ -733,7 +742,8 @@ void twogrid_setup(Geom& g, int q, int coarse_mode) {
   STOKES_CUDA(cudaMemcpyAsync(&hstatus, t.status.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
   STOKES_CUDA(cudaMemcpyAsync(&hbar, t.barrier.get() + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   STOKES_CUDA(cudaStreamSynchronize(s));
-  require(hbar == 0, "two-grid: panel factorisation grid barrier timed out", STOKES_ECUDA);
+  require(hbar == 0, "two-grid: a bounded wait of the coarse LU (panel barrier or tensor-core pipeline) timed out",
+          STOKES_ECUDA);
   require(hstatus == 0, "two-grid: singular coarse operator (zero pivot)", STOKES_EBREAKDOWN);
   std::vector<int> perm(m);
   for (int64_t r = 0; r < m; ++r) perm[r] = (int)r;
@@ -757,7 +767,9 @@ void twogrid_setup(Geom& g, int q, int coarse_mode) {
   t.use_lu = coarse_mode == STOKES_TG_COARSE_LU || (coarse_mode == STOKES_TG_COARSE_AUTO && m > kMaxExplicitCoarse);
   if (t.use_lu) {
     t.inv.release();
-    t.work32.alloc(m);
+    t.work32.alloc(2 * m);
+    t.tinv.alloc(lu_tile_inverse_elems(m));
+    lu_tile_inverses<float>(s, t.lu.get(), m, t.tinv.get());
   } else {
     t.inv.alloc((size_t)m * m);
     invert_from_lu32(g, t.lu.get(), m, t.perm.get(), t.inv.get());
@@ -784,7 +796,8 @@ static void twogrid_apply(Geom& g, const double* r, double* z, const int* done, 
   const int64_t m = 2 * t.Nc;
   const int pc = g.prof.begin(kProfCoarseSolve, 4.0 * (double)m * (double)m, s);
   if (t.use_lu) {
-    lu_solve_persistent<float>(g, t.lu.get(), m, t.perm.get(), t.rc.get(), t.zc.get(), t.work32.get(), done);
+    lu_solve_persistent<float>(g, t.lu.get(), m, t.perm.get(), t.tinv.get(), t.rc.get(), t.zc.get(), t.work32.get(),
+                               done);
   } else {
     k_dense_gemv32_part<<<dim3((unsigned)((m + 1023) / 1024), kGemvSplits), 256, 0, s>>>(
         t.inv.get(), m, t.rc32.get(), t.gemv_part.get(), done);
@@ -810,6 +823,8 @@ void precond_apply(Geom& g, const double* v, double* z, const int* done, bool f3
     const int pb = g.prof.begin(kProfBdApply, coarse + transfers + pores + 32.0 * (double)g.N, g.stream);
     twogrid_apply(g, v, z, done, f32);
     g.prof.end(pb, g.stream);
+  } else if (g.cl.ready) {
+    coarse_apply(g, v, z, done, f32);
   } else {
     bd_apply(g, v, z, done, f32);
   }

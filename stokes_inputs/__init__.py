@@ -36,6 +36,7 @@ __all__ = [
     "cached_geometry",
     "Geometry", "superellipse_curve", "circle_curve", "assemble_geometry",
     "place_pores", "pipe10_geometry", "pipe1000_geometry", "batch_geometry",
+    "coarse_train_geometry", "coarse_eval_geometry", "mlp_initial_params",
     "pipe_bc", "reversed_pipe_bc", "outer_shear_bc", "shear_bc",
     "translation_bc", "rotation_bc", "stokeslet_rotlet_bc",
     "stokeslet_rotlet_velocity", "interior_targets", "random_density",
@@ -229,9 +230,28 @@ def _disc_inside_superellipse(centres, radii, a, b, p, margin):
     return (superellipse_inside(pts, a, b, p) < 1.0).all(1)
 
 
+_CLEARANCE_CACHE = {}
+
+
 def _wall_clearance_grid(a, b, p, h, cap):
     """Cell centres of a grid of spacing h over the wall's bounding box and
-    each centre's distance to the wall, capped at `cap` (negative outside)."""
+    each centre's distance to the wall, capped at `cap` or more (negative
+    outside). The cap only bounds the search: the placement compares these
+    distances with thresholds below `cap`, so a grid computed once with a
+    larger cap serves later calls with the same wall and spacing (read-only)."""
+    key = (float(a), float(b), int(p), float(h))
+    hit = _CLEARANCE_CACHE.get(key)
+    if hit is not None and hit[0] >= cap:
+        return hit[1]
+    cap = max(cap, 0.6)
+    out = _wall_clearance_grid_uncached(a, b, p, h, cap)
+    for arr in out:
+        arr.setflags(write=False)
+    _CLEARANCE_CACHE[key] = (cap, out)
+    return out
+
+
+def _wall_clearance_grid_uncached(a, b, p, h, cap):
     from scipy.spatial import cKDTree
     xs = np.arange(-a + h / 2, a, h)
     ys = np.arange(-b + h / 2, b, h)
@@ -395,6 +415,40 @@ def batch_small_geometry(index: int):
     npp = int(rng.choice([64, 128]))
     no = int(rng.choice([1024, 2048]))
     return batch_geometry(index, n_pores=M, n_per_pore=npp, n_outer=no)
+
+
+def coarse_train_geometry(index: int):
+    """Training geometry `index` of the learned coarse correction: even
+    indices are 1152-node pipes of the pipe10 family (seed 1 + index: 10
+    pores, radii U[0.1, 0.2], 64 nodes per pore, 512 wall nodes); odd ones
+    are longer pipes at the same pore density: M in {20, 30, 40, 50, 60},
+    wall |x/a|^8 + |y|^8 = 1 with a = 0.4 M, centres in |x| < a - 0.8,
+    |y| < 0.6, 64 nodes per pore, 64 * round(0.8 M) wall nodes."""
+    if index % 2 == 0:
+        return pipe10_geometry(1 + index)
+    rng = np.random.default_rng(30_000 + index)
+    M = 20 + 10 * int(rng.integers(0, 5))
+    a = 0.4 * M
+    return _build(30_000 + index, (a, 1.0, 8), 64 * int(round(0.8 * M)),
+                  lambda r, m: r.uniform(0.1, 0.2, m), M, 64, 0.05, (-(a - 0.8), a - 0.8, -0.6, 0.6), False,
+                  {"name": f"coarsetrain{index}"})
+
+
+def coarse_eval_geometry(index: int):
+    """Held-out evaluation geometry `index` (0..99): the 1152-node pipe of
+    the pipe10 family with seed 10000 + index."""
+    return pipe10_geometry(10_000 + index)
+
+
+def mlp_initial_params(seed: int = 0, sizes=((35, 256), (256, 256), (256, 153))) -> np.ndarray:
+    """Initial network parameters, float32, flat in the order W1, b1, W2, b2,
+    W3, b3 (W row-major, fan_in x fan_out): W ~ N(0, 2 / fan_in) (He), b = 0."""
+    rng = np.random.default_rng(777 + seed)
+    parts = []
+    for fi, fo in sizes:
+        parts.append((rng.standard_normal(fi * fo) * math.sqrt(2.0 / fi)).astype(np.float32))
+        parts.append(np.zeros(fo, dtype=np.float32))
+    return np.ascontiguousarray(np.concatenate(parts))
 
 
 # ---------------------------------------------------------------------------

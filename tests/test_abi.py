@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_null_handle_is_rejected_without_gpu(lib):
     assert lib.lib.stokes_geometry_num_nodes(None) == -1
-    assert lib.lib.stokes_precond_setup(None, 1) == lib.STOKES_EINVAL
+    assert lib.lib.stokes_precond_setup(None, 1, None) == lib.STOKES_EINVAL
     assert "null handle" in lib.stokes_last_error()
     assert lib.lib.stokes_geometry_destroy(None) == lib.STOKES_OK
 

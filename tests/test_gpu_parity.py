@@ -446,6 +446,69 @@ def test_two_grid_lu_coarse_solve_matches_dense_oracle(S, dev):
             S.stokes_precond_setup_twogrid_ex(G.handle, 4, 7)
 
 
+def test_two_grid_triangular_solve_with_more_tiles_than_ctas(S, dev):
+    """The persistent triangular solve on a float coarse LU of 11,776 rows
+    (184 tiles of 64 for 152 CTAs, so CTAs own several tiles): two applies
+    give bit-identical results (each CTA's sums run in a fixed order, so a
+    missed wait would show as a difference), and the result agrees with the
+    explicit float inverse formed from the same factors to float rounding
+    times the coarse operator's conditioning (both are float: 1e-2)."""
+    g = si.batch_geometry(3, n_pores=120, n_per_pore=64, n_outer=4096)
+    assert g.n_nodes > 152 * 64
+    v = torch.tensor(si.random_density(g, 8).reshape(-1), device=dev)
+    out = {}
+    for mode in (S.STOKES_TG_COARSE_LU, S.STOKES_TG_COARSE_INVERSE):
+        with S.Geometry(g) as G:
+            S.stokes_precond_setup_twogrid_ex(G.handle, 2, mode)
+            zs = []
+            for _ in range(2):  # the second apply reuses the flags with a new generation
+                z = torch.empty_like(v)
+                S.stokes_precond_apply(G.handle, v, z)
+                zs.append(z)
+            torch.cuda.synchronize()
+            assert torch.equal(zs[0], zs[1])
+            out[mode] = zs[0].cpu().numpy()
+    assert rel(out[S.STOKES_TG_COARSE_LU], out[S.STOKES_TG_COARSE_INVERSE]) < 1e-2
+
+
+def test_block_diagonal_triangular_solve_many_tiles_fp64(S, dev):
+    """The FP64 wall block of a 5000-node wall (10,000 rows: 157 tiles for
+    152 CTAs) applied by the persistent triangular solve equals the oracle's
+    LAPACK block solve."""
+    g = si.assemble_geometry([], si.superellipse_curve(8.0, 1.0, 5000), (8.0, 1.0, 8))
+    v = np.random.default_rng(11).standard_normal(2 * g.n_nodes)
+    ref = O.BlockDiagonal(g).apply(v)
+    with S.Geometry(g) as G:
+        S.stokes_precond_setup(G.handle, S.STOKES_PC_BLOCKDIAG)
+        z = np.empty_like(v)
+        S.stokes_precond_apply(G.handle, v, z)
+    assert rel(z, ref) < 1e-11
+
+
+@pytest.mark.parametrize("which", ["pipe10", "batch120"])
+def test_two_grid_tensor_core_lu_matches_cuda_core_lu(S, dev, which, monkeypatch):
+    """The coarse LU with its trailing updates on the tensor cores (three
+    TF32 products, tcgen05) against the same LU with the CUDA-core float
+    GEMM: the two-grid applies agree to float rounding times the coarse
+    operator's conditioning (1e-3; pivot choices may differ where two
+    candidates tie to rounding)."""
+    g = si.cached_geometry("pipe10", 0) if which == "pipe10" else si.batch_geometry(3, n_pores=120, n_per_pore=64,
+                                                                                      n_outer=4096)
+    v = torch.tensor(si.random_density(g, 9).reshape(-1), device=dev)
+    out = {}
+    for gemm in ("tc", "simt"):
+        if gemm == "simt":
+            monkeypatch.setenv("STOKES_TG_GEMM", "simt")
+        with S.Geometry(g) as G:
+            S.stokes_precond_setup_twogrid_ex(G.handle, 2, S.STOKES_TG_COARSE_INVERSE)
+            z = torch.empty_like(v)
+            S.stokes_precond_apply(G.handle, v, z)
+            torch.cuda.synchronize()
+            out[gemm] = z.cpu().numpy()
+    assert np.isfinite(out["tc"]).all()
+    assert rel(out["tc"], out["simt"]) < 1e-3
+
+
 def test_two_grid_rejects_bad_coarsening(S, dev):
     g = si.pipe10_geometry(0, n_outer=96, n_pores=2, n_per_pore=24)
     with S.Geometry(g) as G:
