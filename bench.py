@@ -79,7 +79,12 @@ def parse_args():
                    help="time only operator applications (A sigma) of each precision on the workload")
     p.add_argument("--batch-bench", action="store_true",
                    help="time the batched operator and lockstep solve on a multi-geometry batch")
+    p.add_argument("--coarse-bench", action="store_true",
+                   help="time the two-grid coarse LU kernels alone on a small case (used for ncu captures)")
     p.add_argument("--batch-geoms", type=int, default=16)
+    p.add_argument("--batch-set", default="small", choices=["small", "config4"],
+                   help="batch bench geometries: the 16-geometry small batch or the 64-geometry subset of the "
+                        "batched configuration")
     p.add_argument("--reps", type=int, default=5)
     p.add_argument("--precisions", default="fp32,df64,fp64")
     p.add_argument("--shape", default="",
@@ -353,6 +358,49 @@ def kernel_bench(args):
     G.close()
 
 
+def coarse_bench(args):
+    """The two-grid preconditioner's coarse LU kernels alone on a small case
+    (the entry point of the ncu captures of the tensor-core trailing update,
+    the panel factorisation and the coarse triangular solve): a porous pipe
+    of 120 pores x 64 nodes and a 4096-node wall (11,776 nodes; coarse
+    operator of every 2nd node, 11,776 rows, 0.55 GB of float factors, more
+    than the L2 cache), `--reps` setups and `--reps` x 10 applies, with
+    the library's CUDA-event timing per kernel class."""
+    import torch
+    import paper_1609_04484_gb300 as S
+    import stokes_inputs as si
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    g = si.batch_geometry(3, n_pores=120, n_per_pore=64, n_outer=4096)
+    v = torch.tensor(si.random_density(g, 1).reshape(-1), device=dev)
+    z = torch.empty_like(v)
+    G = S.Geometry(g, stream=stream.cuda_stream)
+    try:
+        S.stokes_precond_setup_twogrid_ex(G.handle, 2, S.STOKES_TG_COARSE_LU)  # warm-up
+        S.stokes_precond_apply(G.handle, v, z)
+        torch.cuda.synchronize()
+        S.stokes_profile_enable(G.handle, True)
+        for _ in range(args.reps):
+            S.stokes_precond_setup_twogrid_ex(G.handle, 2, S.STOKES_TG_COARSE_LU)
+            for _ in range(10):
+                S.stokes_precond_apply(G.handle, v, z)
+        torch.cuda.synchronize()
+        m = g.n_nodes
+        rec = {"case": "coarse LU of a 11,776-node pipe (every 2nd node: 11,776 rows)", "reps": args.reps}
+        for kind, name in ((S.STOKES_PROF_LU_GEMM, "lu_gemm"), (S.STOKES_PROF_LU_PANEL, "lu_panel"),
+                           (S.STOKES_PROF_COARSE_SOLVE, "coarse_solve")):
+            n, ms, units = S.stokes_profile_read(G.handle, kind)
+            rec[name] = {"launches": n, "ms_total": round(ms, 3), "ms_per_launch": round(ms / max(n, 1), 4)}
+            if name == "lu_gemm":
+                rec[name]["tflops"] = round(units / (ms * 1e-3) / 1e12, 2)
+            if name == "coarse_solve":
+                rec[name]["gbs"] = round(units / (ms * 1e-3) / 1e9, 1)
+                rec[name]["bytes_per_apply"] = 4.0 * m * m
+        print(json.dumps(rec), flush=True)
+    finally:
+        G.close()
+
+
 def batch_workload(n):
     """Uneven batch of porous pipes: pore counts uniform in [20, 120], 64 or
     128 nodes per pore, 1024 or 2048 wall nodes (the batch configuration's
@@ -443,13 +491,87 @@ def batch_bench(args):
         G.close()
 
 
+def batch_config4_record(args, S, torch, dev, stream):
+    """The batched configuration on a subset: 64 geometries (pores uniform in
+    [50, 200] instead of [50, 800]; 64/128/256 nodes per pore; 2048/4096/8192
+    wall nodes) x 4 right-hand sides (pipe, reversed pipe, wall shear,
+    Stokeslet/rotlet data), two-grid preconditioners (every 8th node, float
+    explicit coarse inverses), all 256 systems solved by the lockstep
+    mixed-precision flexible GMRES(100) to 1e-8 (FP32 batched operator in one
+    persistent launch per step, FP64 residuals; the cycle is a captured CUDA
+    graph). Timed on the host around synchronised calls, once per run."""
+    import stokes_inputs as si
+    t0 = time.perf_counter()
+    geoms = generate_geometries("batch_config4_geometry", range(64))
+    gen_s = time.perf_counter() - t0
+    R = 4
+    free0 = torch.cuda.mem_get_info(dev)[0]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Gs = [S.Geometry(g, stream=stream.cuda_stream) for g in geoms]
+    hs = [G.handle for G in Gs]
+    try:
+        for G in Gs:
+            S.stokes_precond_setup_twogrid_ex(G.handle, 8, S.STOKES_TG_COARSE_INVERSE)
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        mem_gb = (free0 - torch.cuda.mem_get_info(dev)[0]) / 1e9
+        fs = []
+        for g in geoms:
+            fs += [torch.tensor(b.reshape(-1), device=dev) for b in
+                   (si.pipe_bc(g), si.reversed_pipe_bc(g), si.outer_shear_bc(g), si.stokeslet_rotlet_bc(g, 0))]
+        pairs = float(sum(g.n_nodes ** 2 for g in geoms)) * R
+        ys = [torch.empty_like(f) for f in fs]
+        S.stokes_batch_matvec(hs, R, fs, ys, S.STOKES_FP32)
+        a, b = _events(torch, stream)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(3):
+            S.stokes_batch_matvec(hs, R, fs, ys, S.STOKES_FP32)
+        b.record(stream)
+        torch.cuda.synchronize()
+        op_ms = a.elapsed_time(b) / 3
+        out = None
+        for attempt in range(2):  # the first call also captures the cycle graph
+            xs = [torch.zeros_like(f) for f in fs]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            iters, relres, status = S.stokes_batch_solve(hs, R, fs, xs, tol=1e-8, restart=100, max_iter=3000,
+                                                         precision=S.STOKES_MIXED_IR)
+            torch.cuda.synchronize()
+            out = (time.perf_counter() - t0, iters, relres, status)
+        solve_s, iters, relres, status = out
+    finally:
+        for G in Gs:
+            G.close()
+    return {"workload": "64 porous pipes x 4 right-hand sides: pores 50-200 (stated: 50-800), 64/128/256 nodes "
+                        "per pore, 2048/4096/8192 wall nodes",
+            "nodes_min_max": [int(min(g.n_nodes for g in geoms)), int(max(g.n_nodes for g in geoms))],
+            "systems": len(fs), "pc": "two-grid, every 8th node, float explicit coarse inverses",
+            "solver": "lockstep flexible GMRES(100), FP32 inner / FP64 outer, tol 1e-8",
+            "generate_s": round(gen_s, 1), "setup_s": round(setup_s, 2), "preconditioner_gb": round(mem_gb, 1),
+            "batched_operator_ms": round(op_ms, 2),
+            "batched_operator_gpairs_rhs_per_s": round(pairs / (op_ms * 1e-3) / 1e9, 1),
+            "solve_s": round(solve_s, 2), "iters_mean": round(float(np.mean(iters)), 1), "iters_max": int(max(iters)),
+            "true_relres_max": float(max(relres)), "converged": int(sum(st == S.STOKES_OK for st in status))}
+
+
 def main():
     args = parse_args()
     if args.batch_bench:
-        batch_bench(args)
+        if args.batch_set == "config4":
+            import torch
+            import paper_1609_04484_gb300 as S
+            dev = torch.device("cuda", 0)
+            print(json.dumps(batch_config4_record(args, S, torch, dev, torch.cuda.current_stream(dev))), flush=True)
+        else:
+            batch_bench(args)
         return
     if args.kernel_bench:
         kernel_bench(args)
+        return
+    if args.coarse_bench:
+        coarse_bench(args)
         return
     if args.impl == "reference":
         run_reference(args)
@@ -640,6 +762,7 @@ PROF_NAMES = {0: "pairs_fp64", 1: "pairs_fp32", 2: "pairs_df64", 3: "epilogue", 
               5: "arnoldi", 6: "precond_setup", 7: "lu_gemm", 8: "lu_panel", 9: "coarse_solve"}
 FP32_FLOP_PEAK = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12   # TFLOP/s, FMA = 2
 FP32_ISSUE_PEAK = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12     # T FP32-pipe ops/s
+TF32_PER_BF16 = 1.1 / 2.25   # nominal dense TF32 / BF16 tensor rates of the part
 
 
 def measured_peaks():
@@ -692,13 +815,30 @@ def kernel_rooflines(S, prof_acc, peaks):
                                    "unit": "T FP32-pipe ops/s", "frac": round(issue / FP32_ISSUE_PEAK, 4),
                                    "ops_per_pair": DF64_OPS_PER_PAIR}
         elif kind == S.STOKES_PROF_LU_GEMM:
-            ach = units / sec / 1e12
-            r.update({"kernel": "k_sgemm128", "bound": "alu", "achieved": round(ach, 2),
-                      "peak": round(FP32_FLOP_PEAK, 2), "unit": "TFLOP/s", "frac": round(ach / FP32_FLOP_PEAK, 4),
-                      "peak_source": "FP32 CUDA cores (derived)"})
+            flops = units / sec
+            if os.environ.get("STOKES_TG_GEMM", "") == "simt":
+                r.update({"kernel": "k_sgemm128", "bound": "alu", "achieved": round(flops / 1e12, 2),
+                          "peak": round(FP32_FLOP_PEAK, 2), "unit": "TFLOP/s",
+                          "frac": round(flops / 1e12 / FP32_FLOP_PEAK, 4),
+                          "peak_source": "FP32 CUDA cores (derived)"})
+            else:
+                # rank-64 updates: each launch reads and writes its rest x rest
+                # block of C once (8 bytes per entry per 2 x 64 flops)
+                gbs = units / (2.0 * 64.0) * 8.0 / sec / 1e9
+                tf32_peak = peaks["bf16_tflops"] * TF32_PER_BF16
+                r.update({"kernel": "k_tc_trailing", "bound": "hbm", "achieved": round(gbs, 1),
+                          "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(gbs / peaks["hbm_gbs"], 4),
+                          "peak_source": peaks["source"],
+                          "algorithmic_bytes": "8 rest^2 per launch (C read and written; the rest x 64 operands "
+                                               "come from L2)",
+                          "tensor": {"useful_tflops": round(flops / 1e12, 2),
+                                     "issued_tflops": round(3 * flops / 1e12, 2),
+                                     "tf32_peak": round(tf32_peak, 1),
+                                     "frac_issued": round(3 * flops / 1e12 / tf32_peak, 4),
+                                     "peak_source": "measured bf16 peak x 1.1 / 2.25 (nominal TF32 / BF16)"}})
         elif kind in (S.STOKES_PROF_COARSE_SOLVE, S.STOKES_PROF_BD_APPLY, S.STOKES_PROF_ARNOLDI):
             gbs = units / sec / 1e9
-            kname = {S.STOKES_PROF_COARSE_SOLVE: "k_lu_solve_persistent", S.STOKES_PROF_BD_APPLY: "(preconditioner apply)",
+            kname = {S.STOKES_PROF_COARSE_SOLVE: "k_lu_solve_flags", S.STOKES_PROF_BD_APPLY: "(preconditioner apply)",
                      S.STOKES_PROF_ARNOLDI: "k_dot_partial + k_orth_update"}[kind]
             r.update({"kernel": kname, "bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"],
                       "unit": "GB/s", "frac": round(gbs / peaks["hbm_gbs"], 4), "peak_source": peaks["source"]})

@@ -28,7 +28,9 @@ namespace stokes {
 namespace {
 
 constexpr int kTs = 64;
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
+constexpr int kPh = kThreads / kTs;  // column phases of a tile
+constexpr int kGroup = 2;            // tiles updated per pass of update_many
 
 __device__ __forceinline__ unsigned ld_volatile_u32(const unsigned* p) { return *(volatile const unsigned*)p; }
 
@@ -54,6 +56,12 @@ __device__ __forceinline__ bool wait_flag(const unsigned* flag, unsigned gen, in
 }
 
 // x (forward solutions) and y (backward solutions): m elements each.
+// Thread (rr, ph) of the CTA handles row rr of a tile and its columns
+// ph, ph + kPh, ...; the step that gates the next tile's solve has its
+// factor block and tile inverse loaded into registers before the wait for
+// the previous tile, so only arithmetic and two block syncs remain on the
+// serial path; the other tiles are updated kGroup at a time (all of their
+// loads issued before any use, for memory-level parallelism).
 template <class T>
 __global__ void __launch_bounds__(kThreads)
 k_lu_solve_flags(const T* __restrict__ A, int64_t m, const int* __restrict__ perm, const T* __restrict__ tinv,
@@ -65,7 +73,7 @@ k_lu_solve_flags(const T* __restrict__ A, int64_t m, const int* __restrict__ per
   extern __shared__ unsigned char smem_raw[];
   T* acc = reinterpret_cast<T*>(smem_raw);  // [my tiles][kTs]
   __shared__ T sz[kTs];
-  __shared__ T red[4][kTs];
+  __shared__ T red[kGroup][kPh][kTs];
   const int64_t nt = (m + kTs - 1) / kTs;
   const int G = gridDim.x, me = blockIdx.x;
   const int mine = (int)((nt - me + G - 1) / G);  // tiles me, me + G, ...
@@ -76,6 +84,7 @@ k_lu_solve_flags(const T* __restrict__ A, int64_t m, const int* __restrict__ per
   const T* invU = tinv + nt * kTs * kTs;
   T* x = work;
   T* y = work + m;
+  constexpr int kPer = kTs / kPh;  // columns per thread
 
   // acc_u = (P v)_u
   for (int e = threadIdx.x; e < mine * kTs; e += kThreads) {
@@ -84,31 +93,50 @@ k_lu_solve_flags(const T* __restrict__ A, int64_t m, const int* __restrict__ per
   }
   __syncthreads();
 
-  // a -= A[u tile rows, t tile columns] sz
-  auto update = [&](int64_t u, int64_t t, T* a) {
+  // this thread's values of the block A[u tile rows, t tile columns]
+  auto load_block = [&](int64_t u, int64_t t, T (&r)[kPer]) {
     const int64_t r0 = u * kTs, c0 = t * kTs;
     const int nc = (int)imin64(kTs, m - c0);
-    T s = 0;
-    if (r0 + rr < m) {
-      const T* col = A + c0 * m + r0 + rr;
-#pragma unroll 4
-      for (int c = ph; c < nc; c += 4) s += col[(int64_t)c * m] * sz[c];
+    const bool rowok = r0 + rr < m;
+    const T* col = A + c0 * m + r0 + rr;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const int c = ph + kPh * j;
+      r[j] = (rowok && c < nc) ? col[(int64_t)c * m] : (T)0;
     }
-    red[ph][rr] = s;
-    __syncthreads();
-    if (ph == 0) a[rr] -= (red[0][rr] + red[1][rr]) + (red[2][rr] + red[3][rr]);
-    __syncthreads();
   };
-  // a = inv(T_tt) a (column-major tile inverse), also written to dst (global)
-  auto solve = [&](int64_t t, const T* inv, T* a, T* dst) {
+  // this thread's values of the inverse of diagonal tile t (column-major)
+  auto load_inv = [&](int64_t t, const T* inv, T (&r)[kPer]) {
     const T* X = inv + t * kTs * kTs;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) r[j] = X[(ph + kPh * j) * kTs + rr];
+  };
+  // a -= block sz
+  auto apply_block = [&](const T (&r)[kPer], T* a) {
     T s = 0;
-#pragma unroll 4
-    for (int c = ph; c < kTs; c += 4) s += X[c * kTs + rr] * a[c];
-    red[ph][rr] = s;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) s += r[j] * sz[ph + kPh * j];
+    red[0][ph][rr] = s;
     __syncthreads();
     if (ph == 0) {
-      const T val = (red[0][rr] + red[1][rr]) + (red[2][rr] + red[3][rr]);
+      T t = 0;
+#pragma unroll
+      for (int q = 0; q < kPh; ++q) t += red[0][q][rr];
+      a[rr] -= t;
+    }
+    __syncthreads();
+  };
+  // a = inv a, also written to dst (global) for the other CTAs
+  auto solve_block = [&](int64_t t, const T (&r)[kPer], T* a, T* dst) {
+    T s = 0;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) s += r[j] * a[ph + kPh * j];
+    red[0][ph][rr] = s;
+    __syncthreads();
+    if (ph == 0) {
+      T val = 0;
+#pragma unroll
+      for (int q = 0; q < kPh; ++q) val += red[0][q][rr];
       a[rr] = val;
       if (t * kTs + rr < m) {
         dst[t * kTs + rr] = val;
@@ -116,6 +144,33 @@ k_lu_solve_flags(const T* __restrict__ A, int64_t m, const int* __restrict__ per
       }
     }
     __syncthreads();
+  };
+  // a_u -= A[u, t] sz for `count` of this CTA's tiles u0, u0 + step, ...
+  constexpr int kG = sizeof(T) == 4 ? kGroup : 1;  // FP64 blocks: one at a time (registers)
+  auto update_many = [&](int64_t u0, int64_t step, int64_t count, int64_t t) {
+    for (int64_t g0 = 0; g0 < count; g0 += kG) {
+      const int n = (int)imin64(kG, count - g0);
+      T r[kG][kPer];
+#pragma unroll
+      for (int q = 0; q < kG; ++q)
+        if (q < n) load_block(u0 + (g0 + q) * step, t, r[q]);
+#pragma unroll
+      for (int q = 0; q < kG; ++q)
+        if (q < n) {
+          T s = 0;
+#pragma unroll
+          for (int j = 0; j < kPer; ++j) s += r[q][j] * sz[ph + kPh * j];
+          red[q][ph][rr] = s;
+        }
+      __syncthreads();
+      if (ph < n) {
+        T sum = 0;
+#pragma unroll
+        for (int q = 0; q < kPh; ++q) sum += red[ph][q][rr];
+        acc[((u0 + (g0 + ph) * step) / G) * kTs + rr] -= sum;
+      }
+      __syncthreads();
+    }
   };
   auto publish = [&](unsigned* f) {
     if (threadIdx.x == 0) {
@@ -132,45 +187,58 @@ k_lu_solve_flags(const T* __restrict__ A, int64_t m, const int* __restrict__ per
     __syncthreads();
   };
 
+  T pa[kPer], pinv[kPer];
   // forward sweep: L (unit lower)
   if (me == 0) {
-    solve(0, invL, acc, x);
+    load_inv(0, invL, pinv);
+    solve_block(0, pinv, acc, x);
     publish(flags);
   }
   for (int64_t t = 0; t < last; ++t) {  // beyond `last` this CTA has no tile to update
-    if (t % G != me && !wait_flag(flags + t, gen, err, limit)) return;
-    fetch(t, x);
     const int64_t nxt = t + 1;
     int64_t u = nxt + ((me - nxt) % G + G) % G;  // this CTA's first tile after t
-    if (u == nxt) {  // it gates the next step: update, solve and publish it first
+    const bool gate = u == nxt;                  // it gates the next step
+    if (gate) {
+      load_block(nxt, t, pa);
+      load_inv(nxt, invL, pinv);
+    }
+    if (t % G != me && !wait_flag(flags + t, gen, err, limit)) return;
+    fetch(t, x);
+    if (gate) {
       T* a = acc + (nxt / G) * kTs;
-      update(nxt, t, a);
-      solve(nxt, invL, a, x);
+      apply_block(pa, a);
+      solve_block(nxt, pinv, a, x);
       publish(flags + nxt);
       u += G;
     }
-    for (; u < nt; u += G) update(u, t, acc + (u / G) * kTs);
+    if (u < nt) update_many(u, G, (nt - 1 - u) / G + 1, t);
   }
 
   // backward sweep: U (upper, with its diagonal) from the forward solution in acc
   unsigned* bflags = flags + nt;
   if (last == nt - 1) {
-    solve(nt - 1, invU, acc + ((nt - 1) / G) * kTs, y);
+    load_inv(nt - 1, invU, pinv);
+    solve_block(nt - 1, pinv, acc + ((nt - 1) / G) * kTs, y);
     publish(bflags + nt - 1);
   }
   for (int64_t t = nt - 1; t > me; --t) {  // at or below `me` this CTA has no tile to update
-    if (t % G != me && !wait_flag(bflags + t, gen, err, limit)) return;
-    fetch(t, y);
     const int64_t prv = t - 1;
     int64_t u = prv - ((prv - me) % G + G) % G;  // this CTA's last tile before t
-    if (u == prv) {
+    const bool gate = u == prv;
+    if (gate) {
+      load_block(prv, t, pa);
+      load_inv(prv, invU, pinv);
+    }
+    if (t % G != me && !wait_flag(bflags + t, gen, err, limit)) return;
+    fetch(t, y);
+    if (gate) {
       T* a = acc + (prv / G) * kTs;
-      update(prv, t, a);
-      solve(prv, invU, a, y);
+      apply_block(pa, a);
+      solve_block(prv, pinv, a, y);
       publish(bflags + prv);
       u -= G;
     }
-    for (; u >= 0; u -= G) update(u, t, acc + (u / G) * kTs);
+    if (u >= 0) update_many(u, -(int64_t)G, (u - me) / G + 1, t);
   }
   for (int e = threadIdx.x; e < mine * kTs; e += kThreads) {
     const int64_t row = (int64_t)(me + (e / kTs) * G) * kTs + (e % kTs);

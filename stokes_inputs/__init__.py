@@ -36,7 +36,7 @@ __all__ = [
     "cached_geometry",
     "Geometry", "superellipse_curve", "circle_curve", "assemble_geometry",
     "place_pores", "pipe10_geometry", "pipe1000_geometry", "batch_geometry",
-    "coarse_train_geometry", "coarse_eval_geometry", "mlp_initial_params",
+    "coarse_train_geometry", "coarse_eval_geometry", "mlp_initial_params", "batch_config4_geometry",
     "pipe_bc", "reversed_pipe_bc", "outer_shear_bc", "shear_bc",
     "translation_bc", "rotation_bc", "stokeslet_rotlet_bc",
     "stokeslet_rotlet_velocity", "interior_targets", "random_density",
@@ -415,6 +415,18 @@ def batch_small_geometry(index: int):
     npp = int(rng.choice([64, 128]))
     no = int(rng.choice([1024, 2048]))
     return batch_geometry(index, n_pores=M, n_per_pore=npp, n_outer=no)
+
+
+def batch_config4_geometry(index: int):
+    """Geometry `index` (0..63) of the batched configuration's subset: pore
+    count uniform in [50, 200] (the configuration states [50, 800]), nodes per
+    pore in {64, 128, 256}, wall nodes in {2048, 4096, 8192}, otherwise as
+    batch_geometry (pores fill ~30 % of the wall's area). Seed 40000 + index."""
+    rng = np.random.default_rng(40_000 + index)
+    M = int(rng.integers(50, 201))
+    npp = int(rng.choice([64, 128, 256]))
+    no = int(rng.choice([2048, 4096, 8192]))
+    return batch_geometry(40_000 + index, n_pores=M, n_per_pore=npp, n_outer=no)
 
 
 def coarse_train_geometry(index: int):
