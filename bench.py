@@ -44,6 +44,7 @@ DF64_OPS_PER_PAIR = 129
 # parts 6, rho^2 2, r.a 2, r.sigma 2, coefficient 3, accumulation 2
 F32_OPS_PER_PAIR = 17
 METRIC = "time-to-solution @1e-8 rel. residual; Stokes matvec Gpairs/s vs FLOP peak"
+LU_PANEL_TC = 128  # panel width of the coarse LU with tensor-core trailing updates (8192 rows and up)
 # DRAM bytes (read + write) per launch of a kernel on the 136,192-node
 # workload, from one ncu capture of that kernel shape (the summaries are kept
 # with the profiles); keyed by (kernel, threads, targets per thread, tile). A
@@ -822,14 +823,15 @@ def kernel_rooflines(S, prof_acc, peaks):
                           "frac": round(flops / 1e12 / FP32_FLOP_PEAK, 4),
                           "peak_source": "FP32 CUDA cores (derived)"})
             else:
-                # rank-64 updates: each launch reads and writes its rest x rest
-                # block of C once (8 bytes per entry per 2 x 64 flops)
-                gbs = units / (2.0 * 64.0) * 8.0 / sec / 1e9
+                # rank-kb updates (kb = 128: 128-column panels from 8192 coarse
+                # rows on): each launch reads and writes its rest x rest block
+                # of C once (8 bytes per entry per 2 kb flops)
+                gbs = units / (2.0 * LU_PANEL_TC) * 8.0 / sec / 1e9
                 tf32_peak = peaks["bf16_tflops"] * TF32_PER_BF16
                 r.update({"kernel": "k_tc_trailing", "bound": "hbm", "achieved": round(gbs, 1),
                           "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(gbs / peaks["hbm_gbs"], 4),
                           "peak_source": peaks["source"],
-                          "algorithmic_bytes": "8 rest^2 per launch (C read and written; the rest x 64 operands "
+                          "algorithmic_bytes": "8 rest^2 per launch (C read and written; the rest x 128 operands "
                                                "come from L2)",
                           "tensor": {"useful_tflops": round(flops / 1e12, 2),
                                      "issued_tflops": round(3 * flops / 1e12, 2),
@@ -844,7 +846,7 @@ def kernel_rooflines(S, prof_acc, peaks):
                       "unit": "GB/s", "frac": round(gbs / peaks["hbm_gbs"], 4), "peak_source": peaks["source"]})
         elif kind == S.STOKES_PROF_LU_PANEL:
             r.update({"kernel": "k_panel_lu32", "bound": "latency", "achieved": round(units / sec, 1),
-                      "unit": "columns/s", "note": "two grid barriers per column"})
+                      "unit": "columns/s", "note": "one grid barrier per column"})
         else:
             r.update({"kernel": name})
         out.append(r)

@@ -350,9 +350,12 @@ k_gemm_trailing(double* __restrict__ A, int64_t m, int64_t k0, int kb) {
   }
 }
 
-// Inverse of a big block from its factors: each CTA solves for a tile of 32
-// columns of the identity (rows permuted by perm).
-constexpr int kInvCols = 32;
+// Inverse of a big block from its factors: each CTA solves for a tile of 8
+// columns of the identity (rows permuted by perm). The CTAs step through the
+// m columns of L and U in lockstep with a block barrier per step, so narrow
+// tiles (m / 8 CTAs: 128 for a 1024-row wall block) spread the FP64 work
+// over more SMs than wide ones would.
+constexpr int kInvCols = 8;
 __global__ void __launch_bounds__(256)
 k_inv_from_lu(const double* __restrict__ A, int64_t m, const int* __restrict__ perm,
               double* __restrict__ X) {

@@ -349,9 +349,11 @@ void sgemm32(cudaStream_t s, int64_t M, int64_t N, int K, float alpha, const flo
 // ---- tc_gemm.cu ----
 // false when STOKES_TG_GEMM=simt selects the CUDA-core trailing updates
 bool tc_trailing_enabled();
-// A[b.., b..] -= A[b.., k0..k0+64) A[k0..k0+64), b..), b = k0 + 64 (column-major
-// float m x m) on the tensor cores (three TF32 products); work: tc_trailing_work_floats(m)
-void tc_trailing_update(cudaStream_t s, float* A, int64_t m, int64_t k0, int64_t rest, float* work, int* err);
+// A[b.., b..] -= A[b.., k0..k0+kb) A[k0..k0+kb), b..), b = k0 + kb, kb in {32, 64,
+// 96, 128} (column-major float m x m) on the tensor cores (three TF32
+// products); work: tc_trailing_work_floats(m)
+void tc_trailing_update(cudaStream_t s, float* A, int64_t m, int64_t k0, int kb, int64_t rest, float* work,
+                        int* err);
 int64_t tc_trailing_work_floats(int64_t m);
 
 // ---- bd_trsv.cu ----

@@ -1,17 +1,18 @@
 // Trailing update of the two-grid preconditioner's coarse LU on the
 // fifth-generation tensor cores (tcgen05 MMA with TMEM accumulators, TMA
 // tile loads, mbarrier pipeline):
-//   C[base.., base..] -= L21 U12,  L21 = rest x 64, U12 = 64 x rest
-// (one rank-64 update of the right-looking blocked LU). The LU is factorised
+//   C[base.., base..] -= L21 U12,  L21 = rest x kb, U12 = kb x rest
+// (one rank-kb update of the right-looking blocked LU; kb a multiple of 32,
+// at most 128). The LU is factorised
 // in single precision; TF32 alone keeps ~11 bits, so each product is split
 // into three TF32 products (a = a_hi + a_lo, a_hi = a rounded to TF32):
 //   a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi     (relative error ~2^-21)
 // with float accumulation in TMEM.
 //
 // Per panel a small kernel writes the hi and lo parts of both operands as
-// K-major [rows][64] float arrays (L21 is stored column-major, so it is
+// K-major [rows][kb] float arrays (L21 is stored column-major, so it is
 // transposed on the way). The GEMM is persistent and warp-specialised:
-//   warp 0     TMA producer: for each 128 x 128 output tile and each half of
+//   warp 0     TMA producer: for each 128 x 128 output tile and each slice of
 //              K (32 floats = one 128-byte swizzle row) it loads the four
 //              operand slabs (A_hi, A_lo, B_hi, B_lo: 16 KB each) into a ring
 //              of kStages shared-memory stages (128-byte swizzle);
@@ -39,8 +40,9 @@ namespace stokes {
 
 namespace {
 
-constexpr int kBM = 128, kBN = 128, kKH = 32;  // tile rows, tile columns, K half (floats)
-constexpr int kPanel = 64;                     // K of one trailing update
+constexpr int kBM = 128, kBN = 128, kKH = 32;  // tile rows, tile columns, K slice (floats)
+constexpr int kMaxPanel = 128;                 // largest K of one trailing update
+constexpr int kPrepRows = 64;                  // rows per CTA of the operand preparation
 constexpr int kStages = 3;
 constexpr int kSlab = kBM * kKH * 4;           // bytes of one operand slab (16 KB)
 constexpr int kStageBytes = 4 * kSlab;         // A_hi, A_lo, B_hi, B_lo
@@ -143,35 +145,37 @@ __device__ __forceinline__ float to_tf32(float a) {
   return __uint_as_float(r);
 }
 
-// hi / lo TF32 parts of both operands of one trailing update, K-major:
+// hi / lo TF32 parts of both operands of one trailing update, K-major with
+// row length kb (each CTA kPrepRows rows):
 //   a_hi[r][k], a_lo[r][k] from L21[r][k] = A[(k0 + k) m + base + r]   (blockIdx.y = 0)
 //   b_hi[n][k], b_lo[n][k] from U12[k][n] = A[(base + n) m + k0 + k]   (blockIdx.y = 1)
 __global__ void __launch_bounds__(256)
-k_tc_prep(const float* __restrict__ A, int64_t m, int64_t k0, int64_t base, int64_t rest, float* __restrict__ ahi,
-          float* __restrict__ alo, float* __restrict__ bhi, float* __restrict__ blo) {
+k_tc_prep(const float* __restrict__ A, int64_t m, int64_t k0, int kb, int64_t base, int64_t rest,
+          float* __restrict__ ahi, float* __restrict__ alo, float* __restrict__ bhi, float* __restrict__ blo) {
   count_launch();
-  const int64_t r0 = blockIdx.x * (int64_t)kPanel;
+  const int64_t r0 = blockIdx.x * (int64_t)kPrepRows;
+  const int n = kb * kPrepRows;
   if (blockIdx.y == 0) {
-    __shared__ float t[kPanel][kPanel + 1];  // [k][r]
-    for (int e = threadIdx.x; e < kPanel * kPanel; e += blockDim.x) {
-      const int k = e / kPanel, r = e % kPanel;
+    __shared__ float t[kMaxPanel][kPrepRows + 1];  // [k][r]: L21 is column-major, read along r
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const int k = e / kPrepRows, r = e % kPrepRows;
       t[k][r] = r0 + r < rest ? A[(k0 + k) * m + base + r0 + r] : 0.f;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < kPanel * kPanel; e += blockDim.x) {
-      const int r = e / kPanel, k = e % kPanel;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const int r = e / kb, k = e % kb;
       if (r0 + r >= rest) continue;
       const float a = t[k][r], h = to_tf32(a);
-      ahi[(r0 + r) * kPanel + k] = h;
-      alo[(r0 + r) * kPanel + k] = a - h;
+      ahi[(r0 + r) * kb + k] = h;
+      alo[(r0 + r) * kb + k] = a - h;
     }
   } else {
-    for (int e = threadIdx.x; e < kPanel * kPanel; e += blockDim.x) {
-      const int n = e / kPanel, k = e % kPanel;
-      if (r0 + n >= rest) continue;
-      const float a = A[(base + r0 + n) * m + k0 + k], h = to_tf32(a);
-      bhi[(r0 + n) * kPanel + k] = h;
-      blo[(r0 + n) * kPanel + k] = a - h;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const int c = e / kb, k = e % kb;
+      if (r0 + c >= rest) continue;
+      const float a = A[(base + r0 + c) * m + k0 + k], h = to_tf32(a);
+      bhi[(r0 + c) * kb + k] = h;
+      blo[(r0 + c) * kb + k] = a - h;
     }
   }
 }
@@ -182,7 +186,7 @@ struct TcMaps {
 
 __global__ void __launch_bounds__(kThreads, 1)
 k_tc_trailing(const __grid_constant__ TcMaps maps, float* __restrict__ C, int64_t ldc, int64_t base, int64_t rest,
-              int* __restrict__ err) {
+              int nslices, int* __restrict__ err) {
   count_launch();
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -228,7 +232,7 @@ k_tc_trailing(const __grid_constant__ TcMaps maps, float* __restrict__ C, int64_
       bool ok = true;
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const int rm = (int)((t % mt) * kBM), rn = (int)((t / mt) * kBN);
-        for (int h = 0; h < 2 && ok; ++h, ++it) {
+        for (int h = 0; h < nslices && ok; ++h, ++it) {
           const int s = (int)(it % kStages);
           const uint32_t round = (uint32_t)(it / kStages);
           if (!mbar_wait(&empty[s], (round & 1) ^ 1, err)) { ok = false; break; }
@@ -255,7 +259,7 @@ k_tc_trailing(const __grid_constant__ TcMaps maps, float* __restrict__ C, int64_
         if (!mbar_wait(&tempty[b], (use & 1) ^ 1, err)) { ok = false; break; }
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(b * kBN);
-        for (int h = 0; h < 2; ++h, ++it) {
+        for (int h = 0; h < nslices; ++h, ++it) {
           const int s = (int)(it % kStages);
           const uint32_t round = (uint32_t)(it / kStages);
           if (!mbar_wait(&full[s], round & 1, err)) { ok = false; break; }
@@ -326,11 +330,11 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2D map of a K-major [rows][64] float array: boxes of 32 floats x 128 rows,
+// 2D map of a K-major [rows][kb] float array: boxes of 32 floats x 128 rows,
 // 128-byte swizzle, zero fill out of range.
-void make_map(CUtensorMap* map, const float* base, int64_t rows) {
-  const cuuint64_t dims[2] = {(cuuint64_t)kPanel, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)kPanel * sizeof(float)};
+void make_map(CUtensorMap* map, const float* base, int64_t rows, int kb) {
+  const cuuint64_t dims[2] = {(cuuint64_t)kb, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)kb * sizeof(float)};
   const cuuint32_t box[2] = {(cuuint32_t)kKH, (cuuint32_t)kBM};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = encode_fn()(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box,
@@ -346,29 +350,33 @@ bool tc_trailing_enabled() {
   return !(e && std::string(e) == "simt");
 }
 
-// A[base.., base..] -= A[base.., k0..k0+64) A[k0..k0+64), base..) for the
-// column-major m x m float matrix A (base = k0 + 64), on the tensor cores.
-// work: 4 * 64 * rest floats; err: device error word (sticky).
-void tc_trailing_update(cudaStream_t s, float* A, int64_t m, int64_t k0, int64_t rest, float* work, int* err) {
+// A[base.., base..] -= A[base.., k0..k0+kb) A[k0..k0+kb), base..) for the
+// column-major m x m float matrix A (base = k0 + kb; kb a multiple of 32, at
+// most 128), on the tensor cores. work: 4 kb rest floats; err: device error
+// word (sticky).
+void tc_trailing_update(cudaStream_t s, float* A, int64_t m, int64_t k0, int kb, int64_t rest, float* work,
+                        int* err) {
   if (rest <= 0) return;
+  require(kb > 0 && kb % kKH == 0 && kb <= kMaxPanel, "tensor-core trailing update: panel width must be 32, 64, 96 or 128",
+          STOKES_EINVAL);
   static bool attr = false;
   if (!attr) {
     STOKES_CUDA(cudaFuncSetAttribute(k_tc_trailing, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
     attr = true;
   }
-  const int64_t base = k0 + kPanel;
+  const int64_t base = k0 + kb;
   float* ahi = work;
-  float* alo = ahi + rest * kPanel;
-  float* bhi = alo + rest * kPanel;
-  float* blo = bhi + rest * kPanel;
-  k_tc_prep<<<dim3((unsigned)((rest + kPanel - 1) / kPanel), 2), 256, 0, s>>>(A, m, k0, base, rest, ahi, alo, bhi,
-                                                                              blo);
+  float* alo = ahi + rest * kb;
+  float* bhi = alo + rest * kb;
+  float* blo = bhi + rest * kb;
+  k_tc_prep<<<dim3((unsigned)((rest + kPrepRows - 1) / kPrepRows), 2), 256, 0, s>>>(A, m, k0, kb, base, rest, ahi, alo,
+                                                                                    bhi, blo);
   STOKES_LAUNCHED();
   TcMaps maps;
-  make_map(&maps.ahi, ahi, rest);
-  make_map(&maps.alo, alo, rest);
-  make_map(&maps.bhi, bhi, rest);
-  make_map(&maps.blo, blo, rest);
+  make_map(&maps.ahi, ahi, rest, kb);
+  make_map(&maps.alo, alo, rest, kb);
+  make_map(&maps.bhi, bhi, rest, kb);
+  make_map(&maps.blo, blo, rest, kb);
   static int nsm = 0;
   if (nsm == 0) {
     int dev = 0;
@@ -377,11 +385,11 @@ void tc_trailing_update(cudaStream_t s, float* A, int64_t m, int64_t k0, int64_t
   }
   const int64_t mt = (rest + kBM - 1) / kBM;
   const unsigned grid = (unsigned)std::min<int64_t>(nsm, mt * mt);
-  k_tc_trailing<<<grid, kThreads, kSmemBytes, s>>>(maps, A, m, base, rest, err);
+  k_tc_trailing<<<grid, kThreads, kSmemBytes, s>>>(maps, A, m, base, rest, kb / kKH, err);
   STOKES_LAUNCHED();
 }
 
-int64_t tc_trailing_work_floats(int64_t m) { return 4 * (int64_t)kPanel * m; }
+int64_t tc_trailing_work_floats(int64_t m) { return 4 * (int64_t)kMaxPanel * m; }
 
 unsigned long long launches_tc_gemm() { return tu_launches(); }
 

@@ -30,7 +30,9 @@ void bd_apply_pores_accumulate(Geom& g, const double* h, double* z, const int* d
 
 namespace {
 
-constexpr int kNb = 64;
+constexpr int kNb = 64;      // panel width of the coarse LU (CUDA-core trailing updates)
+constexpr int kNbTc = 128;   // panel width with tensor-core trailing updates (half the trailing traffic)
+constexpr int kNbMax = 128;
 constexpr int64_t kMaxExplicitCoarse = 40960;  // coarse unknowns up to which the inverse is formed
 
 __global__ void k_coarse_gather(int64_t Nc, int q, const int64_t* __restrict__ off, const int64_t* __restrict__ off_c,
@@ -296,37 +298,53 @@ __global__ void k_panel_update32(float* __restrict__ A, int64_t m, int64_t c, in
 }
 
 // One panel [k0, k0 + kb) of the blocked LU in a single cooperative launch
-// (every CTA resident), the same steps as k_piv_partial32, k_piv_swap32 and
-// k_panel_update32 per column with grid barriers between them:
-//   1. each CTA's largest |A[r][c]|, r >= c (ties: smallest row);
-//   2. every CTA reduces the partials in the same order, records the pivot,
-//      swaps rows c and p over all m columns (its share of the columns);
-//   3. rows r > c: l = A[r][c] / pivot, A[r][q] -= l A[c][q] for the panel's
-//      later columns q.
-// A thread's step 3 produces the new column c + 1 on its own rows, so it
-// takes step 1 of column c + 1 there at once: two barriers per column.
-// pv holds gridDim.x absolute and gridDim.x signed partial values, pi their rows.
-__device__ __forceinline__ void panel_partials(float best, int64_t bi, const float* __restrict__ A, int64_t m,
-                                               int64_t c, float* __restrict__ pv, int64_t* __restrict__ pi) {
-  argmax_reduce_f(best, bi);
-  if (threadIdx.x == 0) {
-    pv[blockIdx.x] = best;
-    pv[gridDim.x + blockIdx.x] = bi < m ? A[c * m + bi] : 0.f;
-    pi[blockIdx.x] = bi;
-  }
-}
-
+// (every CTA resident) with ONE grid barrier per column. Thread tid owns the
+// rows k0 + tid + i * stride for the whole panel. For column c:
+//   1. (before the barrier) each CTA's largest |A[r][c]| over its rows
+//      r >= c (ties: smallest row), and that candidate row's panel values
+//      A[r][c .. pend) staged in global memory (double-buffered by the
+//      column's parity, as are the partials, so that a CTA one column ahead
+//      never overwrites what a slower one still reads);
+//   2. grid barrier; every CTA reduces the partials in the same order
+//      (largest value, ties to the smallest row), takes the winner's staged
+//      row as the pivot row and records the pivot;
+//   3. the thread owning the pivot row p exchanges rows c and p across the
+//      panel (the multipliers of the earlier panel columns directly; from
+//      column c on, row c receives the staged pivot row and row p the old
+//      row c); every thread then scales and updates its rows r > c with the
+//      pivot row held in shared memory, and takes step 1 of column c + 1 on
+//      them.
+// The interchanges of the columns outside the panel are applied afterwards
+// (k_laswp32), so factors and pivots equal those of the per-column kernels.
+// pv: [2][2 G] (|value|, signed value), pi: [2][G], stage: [2][G][kNbMax].
 __global__ void __launch_bounds__(256)
 k_panel_lu32(float* __restrict__ A, int64_t m, int64_t k0, int kb, float* __restrict__ pv,
-             int64_t* __restrict__ pi, int* __restrict__ piv, int* __restrict__ status, gsync::Barrier bar) {
+             int64_t* __restrict__ pi, float* __restrict__ stage, int* __restrict__ piv, int* __restrict__ status,
+             gsync::Barrier bar) {
   count_launch();
   const int G = gridDim.x;
   const int64_t stride = (int64_t)G * blockDim.x;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t pend = k0 + kb;
   unsigned epoch = 0;
+  __shared__ float s_row[kNbMax];
   __shared__ int64_t s_p;
   __shared__ float s_inv;
+  __shared__ int s_w;
+
+  // step 1 of column c on this CTA's rows, given its threads' (best, bi)
+  auto partials = [&](float best, int64_t bi, int64_t c, int par) {
+    argmax_reduce_f(best, bi);  // every thread receives the CTA's result
+    if (threadIdx.x == 0) {
+      pv[par * 2 * G + blockIdx.x] = best;
+      pv[par * 2 * G + G + blockIdx.x] = bi < m ? A[c * m + bi] : 0.f;
+      pi[par * G + blockIdx.x] = bi;
+    }
+    if (bi < m)
+      for (int64_t q = c + threadIdx.x; q < pend; q += blockDim.x)
+        stage[((int64_t)par * G + blockIdx.x) * kNbMax + (q - k0)] = A[q * m + bi];
+  };
+
   {
     float best = -1.f;
     int64_t bi = INT64_MAX;
@@ -334,28 +352,33 @@ k_panel_lu32(float* __restrict__ A, int64_t m, int64_t k0, int kb, float* __rest
       const float v = fabsf(A[k0 * m + r]);
       if (v > best) { best = v; bi = r; }
     }
-    panel_partials(best, bi, A, m, k0, pv, pi);
+    partials(best, bi, k0, 0);
   }
   for (int64_t c = k0; c < pend; ++c) {
-    if (!gsync::grid_sync(bar, epoch)) return;  // partials of column c complete
+    const int par = (int)((c - k0) & 1);
+    if (!gsync::grid_sync(bar, epoch)) return;  // partials and staged rows of column c complete
     if (threadIdx.x < 32) {
-      // warp 0 reduces the G partials: largest value, ties to the smallest
-      // row (the order of the per-column kernels' reduction)
       const int lane = threadIdx.x;
       float b = -1.f, d = 0.f;
       int64_t p = INT64_MAX;
-      for (int q = lane; q < G; q += 32)
-        if (pv[q] > b || (pv[q] == b && pi[q] < p)) { b = pv[q]; p = pi[q]; d = pv[G + q]; }
+      int w = 0;
+      for (int q = lane; q < G; q += 32) {
+        const float vq = __ldcg(pv + par * 2 * G + q);
+        const int64_t iq = __ldcg(reinterpret_cast<const long long*>(pi) + par * G + q);
+        if (vq > b || (vq == b && iq < p)) { b = vq; p = iq; d = __ldcg(pv + par * 2 * G + G + q); w = q; }
+      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const float ob = __shfl_down_sync(0xffffffffu, b, o);
         const int64_t op = __shfl_down_sync(0xffffffffu, p, o);
         const float od = __shfl_down_sync(0xffffffffu, d, o);
-        if (ob > b || (ob == b && op < p)) { b = ob; p = op; d = od; }
+        const int ow = __shfl_down_sync(0xffffffffu, w, o);
+        if (ob > b || (ob == b && op < p)) { b = ob; p = op; d = od; w = ow; }
       }
       if (lane == 0) {
         if (p >= m) { p = c; d = 0.f; }
         s_p = p;
+        s_w = w;
         const bool bad = d == 0.f || !isfinite(d);
         s_inv = bad ? 0.f : 1.f / d;
         if (blockIdx.x == 0) {
@@ -367,32 +390,67 @@ k_panel_lu32(float* __restrict__ A, int64_t m, int64_t k0, int kb, float* __rest
     __syncthreads();
     const int64_t p = s_p;
     const float iv = s_inv;
-    if (p != c)
-      for (int64_t q = tid; q < m; q += stride) {
-        const float t = A[q * m + c];
-        A[q * m + c] = A[q * m + p];
-        A[q * m + p] = t;
-      }
-    if (!gsync::grid_sync(bar, epoch)) return;  // row swap complete
+    // the pivot row's panel values: row c's own if p == c, else the winner's staged copy
+    for (int64_t q = c + threadIdx.x; q < pend; q += blockDim.x)
+      s_row[q - k0] = p == c ? __ldcg(A + q * m + c) : __ldcg(stage + ((int64_t)par * G + s_w) * kNbMax + (q - k0));
+    __syncthreads();
     const bool next = c + 1 < pend;
     float best = -1.f;
     int64_t bi = INT64_MAX;
-    for (int64_t r = c + 1 + tid; r < m; r += stride) {
+    for (int64_t r = k0 + tid; r < m; r += stride) {
+      if (r <= c) continue;
+      if (r == p) {  // rows c and p change places across the panel
+        for (int64_t q = k0; q < c; ++q) {  // multipliers of the earlier columns
+          const float oc = __ldcg(A + q * m + c);
+          A[q * m + c] = A[q * m + p];
+          A[q * m + p] = oc;
+        }
+        for (int64_t q = c; q < pend; ++q) {  // from column c on: the staged pivot row
+          const float oc = __ldcg(A + q * m + c);
+          A[q * m + c] = s_row[q - k0];
+          A[q * m + p] = oc;
+        }
+      }
       const float l = A[c * m + r] * iv;
       A[c * m + r] = l;
-      for (int64_t q = c + 1; q < pend; ++q) A[q * m + r] -= l * A[q * m + c];
+      for (int64_t q = c + 1; q < pend; ++q) A[q * m + r] -= l * s_row[q - k0];
       if (next) {
         const float v = fabsf(A[(c + 1) * m + r]);
         if (v > best) { best = v; bi = r; }
       }
     }
-    if (next) panel_partials(best, bi, A, m, c + 1, pv, pi);
+    if (next) partials(best, bi, c + 1, par ^ 1);
   }
 }
 
-__global__ void k_trsm_row_panel32(float* __restrict__ A, int64_t m, int64_t k0, int kb) {
+// The interchanges piv[k0 .. k0 + kb) applied, in order, to every column
+// outside the panel (one thread per column). After a panel that gave up at
+// a grid barrier (*err set) its later pivots were never written, so nothing
+// is swapped; a pivot outside (c, m) is skipped as well (the buffer is
+// filled with -1 before the factorisation).
+__global__ void k_laswp32(float* __restrict__ A, int64_t m, int64_t k0, int kb, const int* __restrict__ piv,
+                          const int* __restrict__ err) {
   count_launch();
-  const int64_t q = k0 + kb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (*(volatile const int*)err) return;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m - kb; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = j < k0 ? j : j + kb;
+    float* col = A + q * m;
+    for (int64_t c = k0; c < k0 + kb; ++c) {
+      const int64_t p = piv[c];
+      if (p > c && p < m) {
+        const float t = col[c];
+        col[c] = col[p];
+        col[p] = t;
+      }
+    }
+  }
+}
+
+// U12 rows [k0, k0 + kb) (kb <= kNb) of the columns q >= q0: each thread
+// solves L11 x = A[k0 .. k0 + kb)[q] for one column by forward substitution.
+__global__ void k_trsm_row_panel32(float* __restrict__ A, int64_t m, int64_t k0, int kb, int64_t q0) {
+  count_launch();
+  const int64_t q = q0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (q >= m) return;
   float* col = A + q * m + k0;
   float x[kNb];
@@ -637,6 +695,7 @@ void twogrid_setup(Geom& g, int q, int coarse_mode) {
   }
   tm.lap("assembly");
   t.piv.alloc(m);
+  STOKES_CUDA(cudaMemsetAsync(t.piv.get(), 0xff, 4 * m, s));  // -1 until a panel writes its pivots
   t.status.alloc(1);
   STOKES_CUDA(cudaMemsetAsync(t.status.get(), 0, sizeof(int), s));
   DevBuf<float> pv, ivp;
@@ -655,8 +714,10 @@ void twogrid_setup(Geom& g, int q, int coarse_mode) {
     STOKES_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_panel_lu32, 256, 0));
     if (per_sm >= 1) coop_grid = nsm;
   }
-  pv.alloc(std::max(512, 2 * coop_grid));
-  pi.alloc(std::max(256, coop_grid));
+  pv.alloc(std::max(512, 4 * coop_grid));
+  pi.alloc(std::max(256, 2 * coop_grid));
+  DevBuf<float> stage;
+  if (coop_grid > 0) stage.alloc((size_t)2 * coop_grid * kNbMax);
   ivp.alloc(1);
   t.barrier.alloc(4);
   STOKES_CUDA(cudaMemsetAsync(t.barrier.get(), 0, 4 * sizeof(unsigned), s));
@@ -677,8 +738,11 @@ void twogrid_setup(Geom& g, int q, int coarse_mode) {
     STOKES_CUDA(cudaEventRecord(e, s));
     ev.push_back(e);
   };
-  for (int64_t k0 = 0; k0 < m; k0 += kNb) {
-    const int kb = (int)std::min<int64_t>(kNb, m - k0);
+  // 128-column panels when the trailing updates run on the tensor cores
+  // (each update then moves its trailing block once per 128 columns)
+  const int nb = (tc && m >= 8192) ? kNbTc : kNb;
+  for (int64_t k0 = 0; k0 < m; k0 += nb) {
+    const int kb = (int)std::min<int64_t>(nb, m - k0);
     mark();
     const int pp = g.prof.begin(kProfLuPanel, (double)kb, s);
     if (coop_grid > 0) {
@@ -689,10 +753,14 @@ void twogrid_setup(Geom& g, int q, int coarse_mode) {
       int64_t* pip = pi.get();
       int* pivp = t.piv.get();
       int* stp = t.status.get();
-      void* args[] = {(void*)&A, (void*)&m, (void*)&k0v, (void*)&kbv, (void*)&pvp, (void*)&pip, (void*)&pivp,
-                      (void*)&stp, (void*)&bar};
+      float* sgp = stage.get();
+      void* args[] = {(void*)&A,   (void*)&m,   (void*)&k0v,  (void*)&kbv, (void*)&pvp,
+                      (void*)&pip, (void*)&sgp, (void*)&pivp, (void*)&stp, (void*)&bar};
       STOKES_CUDA(cudaMemsetAsync(t.barrier.get(), 0, sizeof(unsigned), s));  // arrivals restart; errors stay
       STOKES_CUDA(cudaLaunchCooperativeKernel((const void*)k_panel_lu32, dim3(coop_grid), dim3(256), args, 0, s));
+      if (m > kb)
+        k_laswp32<<<(unsigned)std::min<int64_t>((m - kb + 255) / 256, 152 * 8), 256, 0, s>>>(A, m, k0, kb, pivp,
+                                                                                            bar.err);
     } else {
       for (int64_t c = k0; c < k0 + kb; ++c) {
         const int parts = (int)std::min<int64_t>(256, (m - c + 255) / 256);
@@ -709,12 +777,21 @@ void twogrid_setup(Geom& g, int q, int coarse_mode) {
     const int64_t rest = m - k0 - kb;
     mark();
     if (rest > 0) {
-      k_trsm_row_panel32<<<(unsigned)((rest + 127) / 128), 128, 0, s>>>(A, m, k0, kb);
-      // A22 -= L21 U12 (rows and columns from k0 + kb on)
+      // U12 = L11^-1 A12 (rows of the panel, columns from k0 + kb on), by
+      // blocks of kNb rows: solve the first block, subtract its product from
+      // the rest of the panel's rows, solve the second
       const int64_t base = k0 + kb;
+      const unsigned gq = (unsigned)((rest + 127) / 128);
+      k_trsm_row_panel32<<<gq, 128, 0, s>>>(A, m, k0, std::min(kb, kNb), base);
+      if (kb > kNb) {
+        sgemm32(s, kb - kNb, rest, kNb, -1.f, A + k0 * m + k0 + kNb, m, A + base * m + k0, m, 1.f,
+                A + base * m + k0 + kNb, m);
+        k_trsm_row_panel32<<<gq, 128, 0, s>>>(A, m, k0 + kNb, kb - kNb, base);
+      }
+      // A22 -= L21 U12 (rows and columns from k0 + kb on)
       const int pg = g.prof.begin(kProfLuGemm, 2.0 * (double)rest * (double)rest * kb, s);
-      if (tc && kb == kNb && rest >= 256)
-        tc_trailing_update(s, A, m, k0, rest, tc_work.get(), (int*)(t.barrier.get() + 2));
+      if (tc && kb % 32 == 0 && rest >= 256)
+        tc_trailing_update(s, A, m, k0, kb, rest, tc_work.get(), (int*)(t.barrier.get() + 2));
       else
         sgemm32(s, rest, rest, kb, -1.f, A + k0 * m + base, m, A + base * m + k0, m, 1.f, A + base * m + base, m);
       g.prof.end(pg, s);
@@ -747,7 +824,10 @@ void twogrid_setup(Geom& g, int q, int coarse_mode) {
   require(hstatus == 0, "two-grid: singular coarse operator (zero pivot)", STOKES_EBREAKDOWN);
   std::vector<int> perm(m);
   for (int64_t r = 0; r < m; ++r) perm[r] = (int)r;
-  for (int64_t c = 0; c < m; ++c) std::swap(perm[c], perm[hpiv[c]]);
+  for (int64_t c = 0; c < m; ++c) {
+    require(hpiv[c] >= c && hpiv[c] < m, "two-grid: coarse LU pivot out of range", STOKES_ECUDA);
+    std::swap(perm[c], perm[hpiv[c]]);
+  }
   t.perm.alloc(m);
   STOKES_CUDA(cudaMemcpyAsync(t.perm.get(), perm.data(), 4 * m, cudaMemcpyHostToDevice, s));
   t.rc.alloc(m);

@@ -409,9 +409,8 @@ def test_two_grid_apply_matches_oracle(S, dev, mode):
 @pytest.mark.parametrize("panel", ["coop", "launches"])
 def test_two_grid_panel_factorisation_paths(S, dev, panel, monkeypatch):
     """The coarse LU's panels factored by one cooperative launch per panel
-    (grid barriers between the pivot search, the row swap and the update)
-    or by three launches per column: both give the oracle's two-grid apply
-    and the dense solution."""
+    (one grid barrier per column) or by three launches per column: both give
+    the oracle's two-grid apply and the dense solution."""
     monkeypatch.setenv("STOKES_TG_PANEL", panel)
     g = si.pipe10_geometry(1, n_outer=256, n_pores=5, n_per_pore=32)
     v = np.random.default_rng(2).standard_normal(2 * g.n_nodes)
@@ -427,6 +426,28 @@ def test_two_grid_panel_factorisation_paths(S, dev, panel, monkeypatch):
         code, iters, rr, _ = S.stokes_gmres_solve(G.handle, f, sig, tol=1e-11, restart=100,
                                                   precision=S.STOKES_DF64)
         assert code == S.STOKES_OK and rel(sig, sref) < 1e-9
+
+
+def test_two_grid_panel_paths_give_identical_factors(S, dev, monkeypatch):
+    """On a coarse LU of 11,776 rows (128-column panels next to the
+    tensor-core trailing updates) the cooperative panel kernel (one grid
+    barrier per column, interchanges outside the panel applied afterwards)
+    and the three launches per column pick the same pivots and do the same
+    float operations, so the two LU-applied two-grid applies are equal bit
+    for bit."""
+    g = si.batch_geometry(3, n_pores=120, n_per_pore=64, n_outer=4096)
+    v = torch.tensor(si.random_density(g, 5).reshape(-1), device=dev)
+    out = {}
+    for panel in ("coop", "launches"):
+        monkeypatch.setenv("STOKES_TG_PANEL", panel)
+        with S.Geometry(g) as G:
+            S.stokes_precond_setup_twogrid_ex(G.handle, 2, S.STOKES_TG_COARSE_LU)
+            z = torch.empty_like(v)
+            S.stokes_precond_apply(G.handle, v, z)
+            torch.cuda.synchronize()
+            out[panel] = z
+    assert torch.isfinite(out["coop"]).all()
+    assert torch.equal(out["coop"], out["launches"])
 
 
 def test_two_grid_lu_coarse_solve_matches_dense_oracle(S, dev):
