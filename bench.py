@@ -51,6 +51,11 @@ LU_PANEL_TC = 128  # panel width of the coarse LU with tensor-core trailing upda
 # kernel or shape not listed, or changed since its capture, reports null.
 MEASURED_TRAFFIC = {("k_dlp_pairs_df64", 256, 1, 256): 9820672.0,
                     ("k_dlp_pairs_f32", 256, 4, 256): 7642624.0}
+# DRAM bytes per algorithmic byte of a kernel whose launches differ in size,
+# from one ncu capture on a smaller case (k_tc_trailing: the 11,392-row update
+# of an 11,776-row coarse LU, 1003.9 MB against 8 rest^2 = 1038.2 MB); the
+# traffic of a launch of the large workload is this ratio times its bytes
+MEASURED_TRAFFIC_RATIO = {"k_tc_trailing": 0.967}
 
 
 def parse_args():
@@ -787,9 +792,11 @@ def kernel_rooflines(S, prof_acc, peaks):
     FLOP peak (152 SMs x 128 lanes x 2 x 2070 MHz = 80.5 TFLOP/s) and, for
     the FP64-class kernels, the multiple of the part's nominal FP64 rate;
     the double-float kernel's FP32-pipe issue use is kept separately. The
-    coarse LU's trailing products: 2 M N K flop against the FP32 CUDA-core
-    peak. The coarse solve: bytes of the factors read per apply against the
-    HBM copy bandwidth."""
+    coarse LU's trailing updates (tensor cores): the bytes of C read and
+    written per launch (8 rest^2) against the HBM copy bandwidth, with the
+    tensor pipe's issued TF32 rate beside (on the CUDA-core GEMM: 2 M N K
+    flop against the FP32 peak). The coarse solve: bytes of the factors read
+    per apply against the HBM copy bandwidth."""
     out = []
     steps = max(1, prof_acc.get("_steps", 1))
     for kind, (n, ms, units) in sorted((k, v) for k, v in prof_acc.items() if isinstance(k, int)):
@@ -833,6 +840,10 @@ def kernel_rooflines(S, prof_acc, peaks):
                           "peak_source": peaks["source"],
                           "algorithmic_bytes": "8 rest^2 per launch (C read and written; the rest x 128 operands "
                                                "come from L2)",
+                          "traffic": round(MEASURED_TRAFFIC_RATIO["k_tc_trailing"] * units / (2.0 * LU_PANEL_TC) * 8.0
+                                           / max(n, 1)),
+                          "traffic_source": "ncu DRAM bytes / algorithmic bytes of one launch on the 11,776-row case "
+                                            "(0.967) times the average launch's algorithmic bytes",
                           "tensor": {"useful_tflops": round(flops / 1e12, 2),
                                      "issued_tflops": round(3 * flops / 1e12, 2),
                                      "tf32_peak": round(tf32_peak, 1),

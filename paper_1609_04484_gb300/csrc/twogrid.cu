@@ -33,6 +33,8 @@ namespace {
 constexpr int kNb = 64;      // panel width of the coarse LU (CUDA-core trailing updates)
 constexpr int kNbTc = 128;   // panel width with tensor-core trailing updates (half the trailing traffic)
 constexpr int kNbMax = 128;
+constexpr int kChunk = 32;       // panel columns a thread moves per pass in the panel kernel
+constexpr int kRedPerLane = 8;   // pivot candidates a lane loads per pass (covers 256 CTAs)
 constexpr int64_t kMaxExplicitCoarse = 40960;  // coarse unknowns up to which the inverse is formed
 
 __global__ void k_coarse_gather(int64_t Nc, int q, const int64_t* __restrict__ off, const int64_t* __restrict__ off_c,
@@ -358,14 +360,29 @@ k_panel_lu32(float* __restrict__ A, int64_t m, int64_t k0, int kb, float* __rest
     const int par = (int)((c - k0) & 1);
     if (!gsync::grid_sync(bar, epoch)) return;  // partials and staged rows of column c complete
     if (threadIdx.x < 32) {
+      // warp 0 reduces the G partials (largest value, ties to the smallest
+      // row); each lane issues all its loads before comparing
       const int lane = threadIdx.x;
       float b = -1.f, d = 0.f;
       int64_t p = INT64_MAX;
       int w = 0;
-      for (int q = lane; q < G; q += 32) {
-        const float vq = __ldcg(pv + par * 2 * G + q);
-        const int64_t iq = __ldcg(reinterpret_cast<const long long*>(pi) + par * G + q);
-        if (vq > b || (vq == b && iq < p)) { b = vq; p = iq; d = __ldcg(pv + par * 2 * G + G + q); w = q; }
+      for (int q0 = 0; q0 < G; q0 += 32 * kRedPerLane) {
+        float vv[kRedPerLane], dd[kRedPerLane];
+        int64_t ii[kRedPerLane];
+#pragma unroll
+        for (int j = 0; j < kRedPerLane; ++j) {
+          const int q = q0 + lane + 32 * j;
+          if (q < G) {
+            vv[j] = __ldcg(pv + par * 2 * G + q);
+            dd[j] = __ldcg(pv + par * 2 * G + G + q);
+            ii[j] = __ldcg(reinterpret_cast<const long long*>(pi) + par * G + q);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < kRedPerLane; ++j) {
+          const int q = q0 + lane + 32 * j;
+          if (q < G && (vv[j] > b || (vv[j] == b && ii[j] < p))) { b = vv[j]; p = ii[j]; d = dd[j]; w = q; }
+        }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -397,26 +414,56 @@ k_panel_lu32(float* __restrict__ A, int64_t m, int64_t k0, int kb, float* __rest
     const bool next = c + 1 < pend;
     float best = -1.f;
     int64_t bi = INT64_MAX;
+    // Rows are moved kChunk columns at a time, all loads of a pass issued
+    // before its stores (one L2 round trip per pass, not per column).
     for (int64_t r = k0 + tid; r < m; r += stride) {
       if (r <= c) continue;
       if (r == p) {  // rows c and p change places across the panel
-        for (int64_t q = k0; q < c; ++q) {  // multipliers of the earlier columns
-          const float oc = __ldcg(A + q * m + c);
-          A[q * m + c] = A[q * m + p];
-          A[q * m + p] = oc;
-        }
-        for (int64_t q = c; q < pend; ++q) {  // from column c on: the staged pivot row
-          const float oc = __ldcg(A + q * m + c);
-          A[q * m + c] = s_row[q - k0];
-          A[q * m + p] = oc;
+        for (int64_t qb = k0; qb < pend; qb += kChunk) {
+          float oc[kChunk], op[kChunk];
+#pragma unroll
+          for (int j = 0; j < kChunk; ++j) {
+            const int64_t q = qb + j;
+            if (q < pend) {
+              oc[j] = __ldcg(A + q * m + c);
+              // the multipliers of the earlier columns from row p itself,
+              // from column c on the staged pivot row
+              op[j] = q < c ? A[q * m + p] : s_row[q - k0];
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < kChunk; ++j) {
+            const int64_t q = qb + j;
+            if (q < pend) {
+              A[q * m + c] = op[j];
+              A[q * m + p] = oc[j];
+            }
+          }
         }
       }
-      const float l = A[c * m + r] * iv;
-      A[c * m + r] = l;
-      for (int64_t q = c + 1; q < pend; ++q) A[q * m + r] -= l * s_row[q - k0];
-      if (next) {
-        const float v = fabsf(A[(c + 1) * m + r]);
-        if (v > best) { best = v; bi = r; }
+      // l = A[r][c] / pivot, A[r][q] -= l A[c][q] for q in (c, pend)
+      float l = 0.f;
+      for (int64_t qb = c; qb < pend; qb += kChunk) {
+        float v[kChunk];
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j)
+          if (qb + j < pend) v[j] = A[(qb + j) * m + r];
+        if (qb == c) {
+          l = v[0] * iv;
+          v[0] = l;
+        }
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) {
+          const int64_t q = qb + j;
+          if (q > c && q < pend) v[j] -= l * s_row[q - k0];
+        }
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j)
+          if (qb + j < pend) A[(qb + j) * m + r] = v[j];
+        if (qb == c && next) {  // the next column's candidate (q = c + 1 is in this pass)
+          const float a = fabsf(v[1]);
+          if (a > best) { best = a; bi = r; }
+        }
       }
     }
     if (next) partials(best, bi, c + 1, par ^ 1);
