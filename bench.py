@@ -501,7 +501,7 @@ def batch_config4_record(args, S, torch, dev, stream):
     """The batched configuration on a subset: 64 geometries (pores uniform in
     [50, 200] instead of [50, 800]; 64/128/256 nodes per pore; 2048/4096/8192
     wall nodes) x 4 right-hand sides (pipe, reversed pipe, wall shear,
-    Stokeslet/rotlet data), two-grid preconditioners (every 8th node, float
+    Stokeslet/rotlet data), two-grid preconditioners (every 4th node, float
     explicit coarse inverses), all 256 systems solved by the lockstep
     mixed-precision flexible GMRES(100) to 1e-8 (FP32 batched operator in one
     persistent launch per step, FP64 residuals; the cycle is a captured CUDA
@@ -518,7 +518,7 @@ def batch_config4_record(args, S, torch, dev, stream):
     hs = [G.handle for G in Gs]
     try:
         for G in Gs:
-            S.stokes_precond_setup_twogrid_ex(G.handle, 8, S.STOKES_TG_COARSE_INVERSE)
+            S.stokes_precond_setup_twogrid_ex(G.handle, 4, S.STOKES_TG_COARSE_INVERSE)
         torch.cuda.synchronize()
         setup_s = time.perf_counter() - t0
         mem_gb = (free0 - torch.cuda.mem_get_info(dev)[0]) / 1e9
@@ -553,7 +553,7 @@ def batch_config4_record(args, S, torch, dev, stream):
     return {"workload": "64 porous pipes x 4 right-hand sides: pores 50-200 (stated: 50-800), 64/128/256 nodes "
                         "per pore, 2048/4096/8192 wall nodes",
             "nodes_min_max": [int(min(g.n_nodes for g in geoms)), int(max(g.n_nodes for g in geoms))],
-            "systems": len(fs), "pc": "two-grid, every 8th node, float explicit coarse inverses",
+            "systems": len(fs), "pc": "two-grid, every 4th node, float explicit coarse inverses",
             "solver": "lockstep flexible GMRES(100), FP32 inner / FP64 outer, tol 1e-8",
             "generate_s": round(gen_s, 1), "setup_s": round(setup_s, 2), "preconditioner_gb": round(mem_gb, 1),
             "batched_operator_ms": round(op_ms, 2),

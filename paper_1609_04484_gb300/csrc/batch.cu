@@ -967,7 +967,9 @@ static void batch_fgmres(Batch& b, int precision, const std::vector<const double
 }
 
 // Mixed precision: outer FP64 residuals per system, inner lockstep FP32
-// cycles to max(1e-4, tol / (2 relres)) on the corrections.
+// cycles to max(1e-4, tol / (2 relres)) on the corrections. Each system
+// has its own budget of max_iter inner iterations: one that stagnates is
+// stopped (STOKES_ENOTCONV) without ending the refinement of the others.
 static void batch_ir(Batch& b, const std::vector<const double*>& f, const std::vector<double>& fnorm, double tol,
                      int max_iter, std::vector<int>& iters, std::vector<double>& relres, std::vector<int>& status) {
   const int S = b.S;
@@ -992,38 +994,40 @@ static void batch_ir(Batch& b, const std::vector<const double*>& f, const std::v
     STOKES_CUDA(cudaMemcpyAsync(b.d_sys.get(), b.sys.data(), S * sizeof(BSys), cudaMemcpyHostToDevice, b.s));
     batch_residuals(b, f, false, rn);
     std::vector<double> itol(S);
-    bool all_conv = true;
+    bool any_live = false;
     double worst = 0.0;
+    int minit = max_iter;  // fewest iterations used by a system still refining
     for (int sidx = 0; sidx < S; ++sidx) {
       relres[sidx] = fnorm[sidx] > 0 ? rn[sidx] / fnorm[sidx] : 0.0;
       if (!std::isfinite(relres[sidx])) status[sidx] = STOKES_EBREAKDOWN;
-      if (relres[sidx] > tol && status[sidx] == STOKES_OK) all_conv = false;
+      if (relres[sidx] > tol && status[sidx] == STOKES_OK) {
+        if (iters[sidx] >= max_iter || outer >= 30) {
+          status[sidx] = STOKES_ENOTCONV;
+        } else {
+          any_live = true;
+          minit = std::min(minit, iters[sidx]);
+        }
+      }
       worst = std::max(worst, relres[sidx]);
       STOKES_CUDA(cudaMemcpyAsync(rpool.get() + off[sidx], b.sys[sidx].r, b.sys[sidx].n * sizeof(double),
                                   cudaMemcpyDeviceToDevice, b.s));
       rptr[sidx] = rpool.get() + off[sidx];
     }
-    if (all_conv) return;
-    int maxit = 0;
-    for (int v : iters) maxit = std::max(maxit, v);
-    if (maxit >= max_iter || outer >= 30) {
-      for (int sidx = 0; sidx < S; ++sidx)
-        if (relres[sidx] > tol && status[sidx] == STOKES_OK) status[sidx] = STOKES_ENOTCONV;
-      return;
-    }
+    if (!any_live) return;
     // inner: A d = r from d = 0; converged systems get tol 1 (no iterations)
     STOKES_CUDA(cudaMemsetAsync(dpool.get(), 0, tot * sizeof(double), b.s));
     std::vector<double> rnorm(S);
     for (int sidx = 0; sidx < S; ++sidx) {
       b.sys[sidx].x = dpool.get() + off[sidx];
       rnorm[sidx] = rn[sidx];
+      // converged or stopped systems take no iterations (tolerance 2)
       itol[sidx] = (relres[sidx] <= tol || status[sidx] != STOKES_OK) ? 2.0
                                                                       : std::max(1e-4, 0.5 * tol / relres[sidx]);
     }
     STOKES_CUDA(cudaMemcpyAsync(b.d_sys.get(), b.sys.data(), S * sizeof(BSys), cudaMemcpyHostToDevice, b.s));
     std::vector<int> it_in, st_in;
     std::vector<double> rr_in;
-    const int cycles = std::max(1, (max_iter - maxit + b.m - 1) / b.m);
+    const int cycles = std::max(1, (max_iter - minit + b.m - 1) / b.m);
     batch_fgmres(b, STOKES_FP32, rptr, rnorm, itol, cycles, true, true, it_in, rr_in, st_in);
     if (std::getenv("STOKES_TRACE"))
       std::fprintf(stderr, "[stokes] batch refinement step %d: worst relres %.3e\n", outer, worst);

@@ -20,9 +20,15 @@
 //              per stage into one of two TMEM accumulators, commits that free
 //              the stage and, after the tile, signal the epilogue;
 //   warps 2-9  epilogue: each warp reads its 32 TMEM lanes (rows) for 64 of
-//              the 128 columns (tcgen05.ld 32x32b) and updates C in place
-//              (for each column, a warp touches 32 consecutive rows: 128
-//              contiguous bytes), then frees the accumulator.
+//              the 128 columns (tcgen05.ld 32x32b), 32 columns at a time,
+//              writes the negated 32 x 32 product to its shared-memory
+//              buffer and adds it to C with one TMA reduction
+//              (cp.reduce.async.bulk.tensor ... add: L2 does the
+//              read-modify-write, so the warp waits on no load of C), then
+//              frees the accumulator. Where C's column stride is not a
+//              multiple of 16 bytes (TMA's rule) the warp instead loads and
+//              stores C itself (for each column, 32 consecutive rows: 128
+//              contiguous bytes).
 // The epilogue of one tile overlaps the loads and MMAs of the next.
 // Every wait is bounded: on timeout the CTA raises the caller's error word,
 // drains its own copies and MMAs (again bounded), frees its TMEM and returns.
@@ -50,7 +56,8 @@ constexpr int kEpiWarps = 8;
 constexpr int kThreads = 32 * (2 + kEpiWarps);
 constexpr int kTmemCols = 2 * kBN;             // two accumulators of 128 columns
 constexpr long long kWaitLimit = 1ll << 22;    // polls of try_wait (each up to ~1 us): seconds at most
-constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + 1024 + 256;
+constexpr int kEpiBuf = 32 * 32;               // floats of one epilogue warp's staging tile (4 KB)
+constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + (size_t)kEpiWarps * kEpiBuf * 4 + 1024 + 256;
 
 static_assert(kBM == kBN, "the operand slabs of A and B have the same shape");
 
@@ -121,6 +128,21 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
                : "memory");
 }
+// C[x.., y..] += the 32 x 32 tile at src (column-major: element (r, c) at
+// src[32 c + r]), x = row, y = column of C; completes through a bulk group.
+__device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap* map, const float* src, int x, int y) {
+  asm volatile("cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                   map),
+               "r"(saddr(src)), "r"(x), "r"(y)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -182,15 +204,17 @@ k_tc_prep(const float* __restrict__ A, int64_t m, int64_t k0, int kb, int64_t ba
 
 struct TcMaps {
   CUtensorMap ahi, alo, bhi, blo;
+  CUtensorMap c;  // the whole matrix, 32 x 32 boxes (used when reduce_c)
 };
 
 __global__ void __launch_bounds__(kThreads, 1)
 k_tc_trailing(const __grid_constant__ TcMaps maps, float* __restrict__ C, int64_t ldc, int64_t base, int64_t rest,
-              int nslices, int* __restrict__ err) {
+              int nslices, int reduce_c, int* __restrict__ err) {
   count_launch();
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)kStages * kStageBytes);
+  float* epi = reinterpret_cast<float*>(smem + (size_t)kStages * kStageBytes);  // [kEpiWarps][kEpiBuf]
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)kStages * kStageBytes + (size_t)kEpiWarps * kEpiBuf * 4);
   uint64_t* empty = full + kStages;
   uint64_t* tfull = empty + kStages;
   uint64_t* tempty = tfull + 2;
@@ -283,6 +307,8 @@ k_tc_trailing(const __grid_constant__ TcMaps maps, float* __restrict__ C, int64_
   } else {  // epilogue warps
     const int g = warp & 3;                 // TMEM lane quarter this warp may read
     const int half = (warp - 2) >> 2;       // columns [64 half, 64 half + 64)
+    float* buf = epi + (warp - 2) * kEpiBuf;
+    bool issued = false;                    // a reduction of this warp may still read buf
     int64_t ti = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++ti) {
       const int b = (int)(ti & 1);
@@ -295,7 +321,25 @@ k_tc_trailing(const __grid_constant__ TcMaps maps, float* __restrict__ C, int64_
       for (int j = 0; j < 2; ++j) {
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(32 * g) << 16) + (uint32_t)(b * kBN + 64 * half + 32 * j), v);
-        if (row < rest) {
+        if (reduce_c) {
+          // a box that starts inside the trailing block may reach past it:
+          // those rows and columns fall outside the map (base + rest = m)
+          // and the TMA unit drops them; a box that starts past it is not
+          // issued
+          if (row - lane < rest && col0 + 32 * j < rest) {
+            if (issued) {
+              if (lane == 0) bulk_wait_read();
+              __syncwarp();
+            }
+#pragma unroll
+            for (int c = 0; c < 32; ++c) buf[32 * c + lane] = -v[c];
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0)
+              tma_reduce_add_2d(&maps.c, buf, (int)(base + row - lane), (int)(base + col0 + 32 * j));
+            issued = true;
+          }
+        } else if (row < rest) {
           float* cp = C + (base + col0 + 32 * j) * ldc + base + row;
           const int ncol = (int)imin64(32, rest - (col0 + 32 * j));
           float old[32];
@@ -310,6 +354,8 @@ k_tc_trailing(const __grid_constant__ TcMaps maps, float* __restrict__ C, int64_
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[b]);
     }
+    if (issued && lane == 0) bulk_wait_all();  // C is complete before the CTA leaves
+    __syncwarp();
   }
   tc_fence_before();
   __syncthreads();
@@ -341,6 +387,20 @@ void make_map(CUtensorMap* map, const float* base, int64_t rows, int kb) {
                                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   require(r == CUDA_SUCCESS, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")", STOKES_ECUDA);
+}
+
+// 2D map of the whole column-major m x m float matrix A (row index
+// innermost): 32 x 32 boxes, no swizzle, for the epilogue's reductions.
+// Needs m * 4 bytes between columns to be a multiple of 16 (m % 4 == 0).
+void make_map_c(CUtensorMap* map, const float* A, int64_t m) {
+  const cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)m};
+  const cuuint64_t strides[1] = {(cuuint64_t)m * sizeof(float)};
+  const cuuint32_t box[2] = {32, 32};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode_fn()(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(A), dims, strides, box,
+                                 estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                 CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  require(r == CUDA_SUCCESS, "cuTensorMapEncodeTiled failed for C (" + std::to_string((int)r) + ")", STOKES_ECUDA);
 }
 
 }  // namespace
@@ -377,6 +437,9 @@ void tc_trailing_update(cudaStream_t s, float* A, int64_t m, int64_t k0, int kb,
   make_map(&maps.alo, alo, rest, kb);
   make_map(&maps.bhi, bhi, rest, kb);
   make_map(&maps.blo, blo, rest, kb);
+  const int reduce_c = (m % 4 == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0) ? 1 : 0;
+  if (reduce_c) make_map_c(&maps.c, A, m);
+  else std::memset(&maps.c, 0, sizeof(maps.c));
   static int nsm = 0;
   if (nsm == 0) {
     int dev = 0;
@@ -385,7 +448,7 @@ void tc_trailing_update(cudaStream_t s, float* A, int64_t m, int64_t k0, int kb,
   }
   const int64_t mt = (rest + kBM - 1) / kBM;
   const unsigned grid = (unsigned)std::min<int64_t>(nsm, mt * mt);
-  k_tc_trailing<<<grid, kThreads, kSmemBytes, s>>>(maps, A, m, base, rest, kb / kKH, err);
+  k_tc_trailing<<<grid, kThreads, kSmemBytes, s>>>(maps, A, m, base, rest, kb / kKH, reduce_c, err);
   STOKES_LAUNCHED();
 }
 

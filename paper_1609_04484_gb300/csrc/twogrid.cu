@@ -35,6 +35,7 @@ constexpr int kNbTc = 128;   // panel width with tensor-core trailing updates (h
 constexpr int kNbMax = 128;
 constexpr int kChunk = 32;       // panel columns a thread moves per pass in the panel kernel
 constexpr int kRedPerLane = 8;   // pivot candidates a lane loads per pass (covers 256 CTAs)
+constexpr int kSubR = 3;         // row slots per thread of the shared-memory panel kernel (64 KB each)
 constexpr int64_t kMaxExplicitCoarse = 40960;  // coarse unknowns up to which the inverse is formed
 
 __global__ void k_coarse_gather(int64_t Nc, int q, const int64_t* __restrict__ off, const int64_t* __restrict__ off_c,
@@ -470,6 +471,187 @@ k_panel_lu32(float* __restrict__ A, int64_t m, int64_t k0, int kb, float* __rest
   }
 }
 
+// A sub-panel [k0, k0 + kb), kb <= kNb, factored in one cooperative launch
+// with its rows held in shared memory: thread t of CTA b owns the rows
+// k0 + 256 b + t + i stride (i < R, stride = 256 G), stored at
+// s_rows[(i kNb + q) 256 + t] for column k0 + q. Per column c:
+//   1. (before the barrier) the CTA's candidate (largest |a[r][c]|, r >= c,
+//      ties to the smallest row) with its whole sub-panel row staged in
+//      global memory, and row c's owner stages row c (both double-buffered
+//      by the column's parity);
+//   2. grid barrier; every CTA reduces the candidates in the same order and
+//      takes the winner's staged row (or row c's, if p == c) as the pivot
+//      row; row c's owner writes the pivot row into row c's slot and row p's
+//      owner writes the old row c into row p's slot;
+//   3. every thread scales and updates its rows r > c in shared memory and
+//      takes step 1 of column c + 1.
+// The rows go back to global memory at the end; the interchanges of the
+// other columns follow (k_laswp32). Each entry sees the same operations as
+// in the per-column kernels, so the factors are the same bit for bit.
+// pv: [2][2 G], pi: [2][G], stage: [2][G][kNb], rowc: [2][kNb].
+__global__ void __launch_bounds__(256)
+k_panel_lu32_smem(float* __restrict__ A, int64_t m, int64_t k0, int kb, int R, float* __restrict__ pv,
+                  int64_t* __restrict__ pi, float* __restrict__ stage, float* __restrict__ rowc,
+                  int* __restrict__ piv, int* __restrict__ status, gsync::Barrier bar) {
+  count_launch();
+  extern __shared__ float s_rows[];  // [R][kNb][256]
+  __shared__ float s_piv[kNb];
+  __shared__ int64_t s_p;
+  __shared__ float s_inv;
+  __shared__ int s_w;
+  const int G = gridDim.x;
+  const int t = threadIdx.x;
+  const int64_t stride = (int64_t)G * 256;
+  const int64_t rbase = k0 + (int64_t)blockIdx.x * 256 + t;  // this thread's row in slot i: rbase + i stride
+  const int64_t pend = k0 + kb;
+  unsigned epoch = 0;
+  auto at = [&](int i, int q, int tt) -> float& { return s_rows[((int64_t)i * kNb + q) * 256 + tt]; };
+  // slot (i, CTA, thread) of row r >= k0
+  auto slot = [&](int64_t r, int& i, int& cta, int& tt) {
+    const int64_t off = r - k0;
+    i = (int)(off / stride);
+    const int64_t rem = off - (int64_t)i * stride;
+    cta = (int)(rem / 256);
+    tt = (int)(rem - (int64_t)cta * 256);
+  };
+
+  for (int i = 0; i < R; ++i) {
+    const int64_t r = rbase + i * stride;
+    for (int q = 0; q < kb; ++q) at(i, q, t) = r < m ? A[(k0 + q) * m + r] : 0.f;
+  }
+  __syncthreads();
+
+  // step 1 of column c (local cc) from the threads' (best, bi)
+  auto candidates = [&](float best, int64_t bi, int64_t c, int par) {
+    argmax_reduce_f(best, bi);  // every thread receives the CTA's result (and the block is in step)
+    const int cc = (int)(c - k0);
+    if (bi < m) {
+      int ib, cb, tb;
+      slot(bi, ib, cb, tb);
+      if (t == 0) {
+        pv[par * 2 * G + blockIdx.x] = best;
+        pv[par * 2 * G + G + blockIdx.x] = at(ib, cc, tb);
+        pi[par * G + blockIdx.x] = bi;
+      }
+      if (t < kb) stage[((int64_t)par * G + blockIdx.x) * kNb + t] = at(ib, t, tb);
+    } else if (t == 0) {
+      pv[par * 2 * G + blockIdx.x] = -1.f;
+      pv[par * 2 * G + G + blockIdx.x] = 0.f;
+      pi[par * G + blockIdx.x] = INT64_MAX;
+    }
+    int ic, cc_cta, tc;
+    slot(c, ic, cc_cta, tc);
+    if (cc_cta == (int)blockIdx.x && t < kb) rowc[par * kNb + t] = at(ic, t, tc);
+  };
+
+  {
+    float best = -1.f;
+    int64_t bi = INT64_MAX;
+    for (int i = 0; i < R; ++i) {
+      const int64_t r = rbase + i * stride;
+      if (r < m) {
+        const float v = fabsf(at(i, 0, t));
+        if (v > best) { best = v; bi = r; }
+      }
+    }
+    candidates(best, bi, k0, 0);
+  }
+  for (int64_t c = k0; c < pend; ++c) {
+    const int cc = (int)(c - k0);
+    const int par = cc & 1;
+    if (!gsync::grid_sync(bar, epoch)) return;  // candidates, staged rows and row c complete
+    if (t < 32) {
+      const int lane = t;
+      float b = -1.f, d = 0.f;
+      int64_t p = INT64_MAX;
+      int w = 0;
+      for (int q0 = 0; q0 < G; q0 += 32 * kRedPerLane) {
+        float vv[kRedPerLane], dd[kRedPerLane];
+        int64_t ii[kRedPerLane];
+#pragma unroll
+        for (int j = 0; j < kRedPerLane; ++j) {
+          const int q = q0 + lane + 32 * j;
+          if (q < G) {
+            vv[j] = __ldcg(pv + par * 2 * G + q);
+            dd[j] = __ldcg(pv + par * 2 * G + G + q);
+            ii[j] = __ldcg(reinterpret_cast<const long long*>(pi) + par * G + q);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < kRedPerLane; ++j) {
+          const int q = q0 + lane + 32 * j;
+          if (q < G && (vv[j] > b || (vv[j] == b && ii[j] < p))) { b = vv[j]; p = ii[j]; d = dd[j]; w = q; }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_down_sync(0xffffffffu, b, o);
+        const int64_t op = __shfl_down_sync(0xffffffffu, p, o);
+        const float od = __shfl_down_sync(0xffffffffu, d, o);
+        const int ow = __shfl_down_sync(0xffffffffu, w, o);
+        if (ob > b || (ob == b && op < p)) { b = ob; p = op; d = od; w = ow; }
+      }
+      if (lane == 0) {
+        if (p >= m) { p = c; d = 0.f; }
+        s_p = p;
+        s_w = w;
+        const bool bad = d == 0.f || !isfinite(d);
+        s_inv = bad ? 0.f : 1.f / d;
+        if (blockIdx.x == 0) {
+          piv[c] = (int)p;
+          if (bad) atomicExch(status, 1);
+        }
+      }
+    }
+    __syncthreads();
+    const int64_t p = s_p;
+    const float iv = s_inv;
+    if (t < kb) {
+      const float oc = __ldcg(rowc + par * kNb + t);  // row c before the exchange
+      const float pr = p == c ? oc : __ldcg(stage + ((int64_t)par * G + s_w) * kNb + t);
+      s_piv[t] = pr;
+      if (p != c) {
+        int i1, b1, t1;
+        slot(c, i1, b1, t1);
+        if (b1 == (int)blockIdx.x) at(i1, t, t1) = pr;  // row c becomes the pivot row
+        slot(p, i1, b1, t1);
+        if (b1 == (int)blockIdx.x) at(i1, t, t1) = oc;  // row p takes the old row c
+      }
+    }
+    __syncthreads();
+    const bool next = c + 1 < pend;
+    float best = -1.f;
+    int64_t bi = INT64_MAX;
+    for (int i = 0; i < R; ++i) {
+      const int64_t r = rbase + i * stride;
+      if (r <= c || r >= m) continue;
+      const float l = at(i, cc, t) * iv;
+      at(i, cc, t) = l;
+      // kChunk columns per pass: loads of a pass before its stores
+      for (int qb = cc + 1; qb < kb; qb += kChunk) {
+        float v[kChunk];
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j)
+          if (qb + j < kb) v[j] = at(i, qb + j, t);
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j)
+          if (qb + j < kb) at(i, qb + j, t) = v[j] - l * s_piv[qb + j];
+      }
+      if (next) {
+        const float a = fabsf(at(i, cc + 1, t));
+        if (a > best) { best = a; bi = r; }
+      }
+    }
+    if (next) candidates(best, bi, c + 1, par ^ 1);
+  }
+  __syncthreads();
+  for (int i = 0; i < R; ++i) {
+    const int64_t r = rbase + i * stride;
+    if (r < m)
+      for (int q = 0; q < kb; ++q) A[(k0 + q) * m + r] = at(i, q, t);
+  }
+}
+
 // The interchanges piv[k0 .. k0 + kb) applied, in order, to every column
 // outside the panel (one thread per column). After a panel that gave up at
 // a grid barrier (*err set) its later pivots were never written, so nothing
@@ -493,12 +675,13 @@ __global__ void k_laswp32(float* __restrict__ A, int64_t m, int64_t k0, int kb, 
   }
 }
 
-// U12 rows [k0, k0 + kb) (kb <= kNb) of the columns q >= q0: each thread
-// solves L11 x = A[k0 .. k0 + kb)[q] for one column by forward substitution.
-__global__ void k_trsm_row_panel32(float* __restrict__ A, int64_t m, int64_t k0, int kb, int64_t q0) {
+// U12 rows [k0, k0 + kb) (kb <= kNb) of the columns q0 <= q < q1: each
+// thread solves L11 x = A[k0 .. k0 + kb)[q] for one column by forward
+// substitution.
+__global__ void k_trsm_row_panel32(float* __restrict__ A, int64_t m, int64_t k0, int kb, int64_t q0, int64_t q1) {
   count_launch();
   const int64_t q = q0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (q >= m) return;
+  if (q >= q1) return;
   float* col = A + q * m + k0;
   float x[kNb];
 #pragma unroll
@@ -761,10 +944,23 @@ void twogrid_setup(Geom& g, int q, int coarse_mode) {
     STOKES_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_panel_lu32, 256, 0));
     if (per_sm >= 1) coop_grid = nsm;
   }
+  // the shared-memory sub-panel kernel: up to kSubR row slots of 64 KB per
+  // CTA (rows below the sub-panel's first: up to kSubR * 256 * grid)
+  bool smem_panel = false;
+  if (coop_grid > 0) {
+    const int bytes = kSubR * kNb * 256 * (int)sizeof(float);
+    STOKES_CUDA(cudaFuncSetAttribute(k_panel_lu32_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    int per_sm = 0;
+    STOKES_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_panel_lu32_smem, 256, bytes));
+    smem_panel = per_sm >= 1;
+  }
   pv.alloc(std::max(512, 4 * coop_grid));
   pi.alloc(std::max(256, 2 * coop_grid));
-  DevBuf<float> stage;
-  if (coop_grid > 0) stage.alloc((size_t)2 * coop_grid * kNbMax);
+  DevBuf<float> stage, rowc;
+  if (coop_grid > 0) {
+    stage.alloc((size_t)2 * coop_grid * kNbMax);
+    rowc.alloc(2 * kNb);
+  }
   ivp.alloc(1);
   t.barrier.alloc(4);
   STOKES_CUDA(cudaMemsetAsync(t.barrier.get(), 0, 4 * sizeof(unsigned), s));
@@ -788,28 +984,40 @@ void twogrid_setup(Geom& g, int q, int coarse_mode) {
   // 128-column panels when the trailing updates run on the tensor cores
   // (each update then moves its trailing block once per 128 columns)
   const int nb = (tc && m >= 8192) ? kNbTc : kNb;
-  for (int64_t k0 = 0; k0 < m; k0 += nb) {
-    const int kb = (int)std::min<int64_t>(nb, m - k0);
-    mark();
-    const int pp = g.prof.begin(kProfLuPanel, (double)kb, s);
+  // One sub-panel [ks, ks + ws), ws <= kNb: pivots piv[ks .. ks + ws) and the
+  // rows exchanged across all m columns. Cooperative kernels (shared-memory
+  // rows where they fit, else global) plus k_laswp32 for the other columns,
+  // or three launches per column; the factors are the same bit for bit.
+  auto factor_subpanel = [&](int64_t ks, int ws) {
     if (coop_grid > 0) {
       gsync::Barrier bar{t.barrier.get(), t.barrier.get() + 1, (int*)(t.barrier.get() + 2), gsync::spin_limit()};
-      int64_t k0v = k0;
-      int kbv = kb;
+      int64_t ksv = ks;
+      int wsv = ws;
       float* pvp = pv.get();
       int64_t* pip = pi.get();
       int* pivp = t.piv.get();
       int* stp = t.status.get();
       float* sgp = stage.get();
-      void* args[] = {(void*)&A,   (void*)&m,   (void*)&k0v,  (void*)&kbv, (void*)&pvp,
-                      (void*)&pip, (void*)&sgp, (void*)&pivp, (void*)&stp, (void*)&bar};
+      float* rcp = rowc.get();
+      const int64_t stride = (int64_t)coop_grid * 256;
+      int R = (int)((m - ks + stride - 1) / stride);
       STOKES_CUDA(cudaMemsetAsync(t.barrier.get(), 0, sizeof(unsigned), s));  // arrivals restart; errors stay
-      STOKES_CUDA(cudaLaunchCooperativeKernel((const void*)k_panel_lu32, dim3(coop_grid), dim3(256), args, 0, s));
-      if (m > kb)
-        k_laswp32<<<(unsigned)std::min<int64_t>((m - kb + 255) / 256, 152 * 8), 256, 0, s>>>(A, m, k0, kb, pivp,
+      if (smem_panel && R <= kSubR) {
+        void* args[] = {(void*)&A,   (void*)&m,   (void*)&ksv, (void*)&wsv,  (void*)&R,   (void*)&pvp,
+                        (void*)&pip, (void*)&sgp, (void*)&rcp, (void*)&pivp, (void*)&stp, (void*)&bar};
+        STOKES_CUDA(cudaLaunchCooperativeKernel((const void*)k_panel_lu32_smem, dim3(coop_grid), dim3(256), args,
+                                                (size_t)R * kNb * 256 * sizeof(float), s));
+      } else {
+        void* args[] = {(void*)&A,   (void*)&m,   (void*)&ksv,  (void*)&wsv, (void*)&pvp,
+                        (void*)&pip, (void*)&sgp, (void*)&pivp, (void*)&stp, (void*)&bar};
+        STOKES_CUDA(
+            cudaLaunchCooperativeKernel((const void*)k_panel_lu32, dim3(coop_grid), dim3(256), args, 0, s));
+      }
+      if (m > ws)
+        k_laswp32<<<(unsigned)std::min<int64_t>((m - ws + 255) / 256, 152 * 8), 256, 0, s>>>(A, m, ks, ws, pivp,
                                                                                             bar.err);
     } else {
-      for (int64_t c = k0; c < k0 + kb; ++c) {
+      for (int64_t c = ks; c < ks + ws; ++c) {
         const int parts = (int)std::min<int64_t>(256, (m - c + 255) / 256);
         k_piv_partial32<<<parts, 256, 0, s>>>(A, m, c, pv.get(), pi.get());
         k_piv_swap32<<<(unsigned)std::min<int64_t>(64, (m + 255) / 256), 256, 0, s>>>(
@@ -817,7 +1025,24 @@ void twogrid_setup(Geom& g, int q, int coarse_mode) {
         const int64_t nr = m - c - 1;
         if (nr > 0)
           k_panel_update32<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(1024, (nr + 127) / 128)), 128, 0,
-                             s>>>(A, m, c, k0 + kb, ivp.get());
+                             s>>>(A, m, c, ks + ws, ivp.get());
+      }
+    }
+  };
+  for (int64_t k0 = 0; k0 < m; k0 += nb) {
+    const int kb = (int)std::min<int64_t>(nb, m - k0);
+    mark();
+    const int pp = g.prof.begin(kProfLuPanel, (double)kb, s);
+    // the panel as sub-panels of kNb columns; after each, the panel's
+    // columns to its right get their rows of U (row-panel solve) and the
+    // product of the sub-panel's L and those rows subtracted below
+    for (int64_t ks = k0; ks < k0 + kb; ks += kNb) {
+      const int ws = (int)std::min<int64_t>(kNb, k0 + kb - ks);
+      factor_subpanel(ks, ws);
+      const int64_t q0 = ks + ws, q1 = k0 + kb;
+      if (q1 > q0) {
+        k_trsm_row_panel32<<<(unsigned)((q1 - q0 + 127) / 128), 128, 0, s>>>(A, m, ks, ws, q0, q1);
+        sgemm32(s, m - q0, q1 - q0, ws, -1.f, A + ks * m + q0, m, A + q0 * m + ks, m, 1.f, A + q0 * m + q0, m);
       }
     }
     g.prof.end(pp, s);
@@ -829,11 +1054,11 @@ void twogrid_setup(Geom& g, int q, int coarse_mode) {
       // the rest of the panel's rows, solve the second
       const int64_t base = k0 + kb;
       const unsigned gq = (unsigned)((rest + 127) / 128);
-      k_trsm_row_panel32<<<gq, 128, 0, s>>>(A, m, k0, std::min(kb, kNb), base);
+      k_trsm_row_panel32<<<gq, 128, 0, s>>>(A, m, k0, std::min(kb, kNb), base, m);
       if (kb > kNb) {
         sgemm32(s, kb - kNb, rest, kNb, -1.f, A + k0 * m + k0 + kNb, m, A + base * m + k0, m, 1.f,
                 A + base * m + k0 + kNb, m);
-        k_trsm_row_panel32<<<gq, 128, 0, s>>>(A, m, k0 + kNb, kb - kNb, base);
+        k_trsm_row_panel32<<<gq, 128, 0, s>>>(A, m, k0 + kNb, kb - kNb, base, m);
       }
       // A22 -= L21 U12 (rows and columns from k0 + kb on)
       const int pg = g.prof.begin(kProfLuGemm, 2.0 * (double)rest * (double)rest * kb, s);

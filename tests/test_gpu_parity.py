@@ -527,6 +527,29 @@ def test_two_grid_tensor_core_lu_matches_cuda_core_lu(S, dev, monkeypatch):
     assert rel(out["tc"], out["simt"]) < 1e-3
 
 
+def test_two_grid_tensor_core_lu_unaligned_column_stride(S, dev, monkeypatch):
+    """A coarse LU of 346 rows (173 coarse nodes: 1384-byte columns, not a
+    multiple of 16, so the tensor-core update's epilogue loads and stores C
+    itself instead of reducing into it through TMA): the two-grid applies
+    with tensor-core and CUDA-core trailing updates agree to 1e-3, and both
+    match the oracle's two-grid apply to the same tolerance."""
+    g = si.pipe10_geometry(2, n_outer=256, n_pores=5, n_per_pore=18)
+    assert (g.n_nodes // 2) % 2 == 1
+    v = np.random.default_rng(4).standard_normal(2 * g.n_nodes)
+    ref = O.TwoGrid(g, 2).apply(v)
+    out = {}
+    for gemm in ("tc", "simt"):
+        if gemm == "simt":
+            monkeypatch.setenv("STOKES_TG_GEMM", "simt")
+        with S.Geometry(g) as G:
+            S.stokes_precond_setup_twogrid_ex(G.handle, 2, S.STOKES_TG_COARSE_INVERSE)
+            z = np.empty_like(v)
+            S.stokes_precond_apply(G.handle, v, z)
+            out[gemm] = z
+    assert rel(out["tc"], out["simt"]) < 1e-3
+    assert rel(out["tc"], ref) < 1e-3
+
+
 def test_two_grid_tensor_core_lu_solve_on_many_tiles(S, dev, monkeypatch):
     """On a 11,776-node geometry (coarse LU of 11,776 rows, 92 x 92 output
     tiles per early trailing update, several per CTA) the coarse operator is
