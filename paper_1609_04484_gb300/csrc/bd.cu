@@ -592,8 +592,10 @@ static void bd_setup_impl(Geom& g, bool skip_wall) {
   }
   if (tri_total) {
     b.lu32.alloc(tri_total);
-    b.work32.alloc(2 * tri_max);
-    b.work64.alloc(2 * tri_max);
+    const int64_t words = lu_solve_work_words(tri_max, sizeof(double));
+    b.trsv_work.alloc(words);
+    STOKES_CUDA(cudaMemsetAsync(b.trsv_work.get(), 0, words * sizeof(unsigned long long), s));
+    b.trsv_gen = 0;
     b.tinv_off.assign(nc, -1);
     int64_t ti_total = 0;
     for (int k : b.tri_ids) {
@@ -650,7 +652,8 @@ void bd_apply(Geom& g, const double* v, double* z, const int* done, bool f32) {
       const int64_t m = b.rows[k];
       const int64_t o = 2 * g.off[k];
       lu_solve_persistent<double>(g, b.lu.get() + b.elem_off[k], m, b.perm.get() + b.piv_off[k],
-                                  b.tinv64.get() + b.tinv_off[k], v + o, z + o, b.work64.get(), done);
+                                  b.tinv64.get() + b.tinv_off[k], v + o, z + o, b.trsv_work.get(), b.trsv_gen,
+                                  done);
     }
   }
   g.prof.end(pb, s);

@@ -6,19 +6,24 @@
 // belongs to CTA u mod gridDim.x, which keeps the tile's running right-hand
 // side in shared memory. The inverses of the diagonal tiles are formed once
 // at setup (lu_tile_inverses), so solving a tile is one small product.
-// Forward sweep over t = 0, 1, ...: the owner of tile t publishes x_t
-// (global memory, then a per-tile flag carrying this launch's generation
-// number); every CTA waits for the flag of t, then subtracts L[u, t] x_t from
+// Forward sweep over t = 0, 1, ...: the owner of tile t publishes x_t, each
+// value in 64-bit words that carry this launch's generation number in their
+// upper half (a float in one word, a double in two); every CTA waits until
+// the words of tile t carry the generation, then subtracts L[u, t] x_t from
 // each of its tiles u > t, the owner of t + 1 first, which solves and
-// publishes t + 1 at once: the chain of dependent tile solves is the only
-// serial part, and the other updates stream the factors at the memory's
-// rate behind it. The backward sweep mirrors it with U from the last tile.
+// publishes t + 1 at once. A 64-bit store is seen whole or not at all, so the
+// word that shows the generation holds the value: no fence, flag or second
+// load sits on the chain of dependent tile solves, the only serial part; the
+// other updates stream the factors at the memory's rate behind it. The
+// owner of the next tile polls all of the tile's words, other CTAs one word
+// with one thread before reading the rest (fewer polls of the same lines).
+// The backward sweep mirrors it with U from the last tile.
 //
-// Every wait on a flag polls with an iteration limit: on timeout the CTA
-// raises the sticky error word, every other CTA sees it at its next poll
-// and leaves, and the host reports the failure instead of hanging. All
-// CTAs are resident (cooperative launch, one CTA per SM), so a flag that
-// will be set is always set by a running CTA.
+// Every wait polls with an iteration limit: on timeout the CTA raises the
+// sticky error word, every other CTA sees it at its next check and leaves,
+// and the host reports the failure instead of hanging. All CTAs are
+// resident (cooperative launch, one CTA per SM), so a value that will be
+// published is always published by a running CTA.
 #include <algorithm>
 
 #include "grid_sync.cuh"
@@ -32,48 +37,71 @@ constexpr int kThreads = 512;
 constexpr int kPh = kThreads / kTs;  // column phases of a tile
 constexpr int kGroup = 2;            // tiles updated per pass of update_many
 
-__device__ __forceinline__ unsigned ld_volatile_u32(const unsigned* p) { return *(volatile const unsigned*)p; }
+typedef unsigned long long u64;
 
-// Wait (thread 0) until flag == gen; false if this or another CTA gave up.
-__device__ __forceinline__ bool wait_flag(const unsigned* flag, unsigned gen, int* err, long long limit) {
-  __shared__ int s_ok;
-  if (threadIdx.x == 0) {
-    long long spins = 0;
-    int ok = 1;
-    while (ld_volatile_u32(flag) != gen) {
-      if (++spins > limit || *(volatile int*)err) {
-        atomicExch(err, 1);
-        ok = 0;
-        break;
-      }
-      __nanosleep(20);
+__device__ __forceinline__ u64 ld_volatile_u64(const u64* p) { return *(volatile const u64*)p; }
+
+// Wait until word p carries generation gen and return it; false on timeout
+// (raising *err) or when another CTA raised *err.
+__device__ __forceinline__ bool wait_word(const u64* p, unsigned gen, int* err, long long limit, u64& w) {
+  long long spins = 0;
+  while (((w = ld_volatile_u64(p)) >> 32) != gen) {
+    if (++spins > limit || ((spins & 63) == 0 && *(volatile int*)err)) {
+      atomicExch(err, 1);
+      return false;
     }
-    __threadfence();
-    s_ok = ok;
+    __nanosleep(20);
   }
-  __syncthreads();
-  return s_ok != 0;
+  return true;
 }
 
-// x (forward solutions) and y (backward solutions): m elements each.
+// Value val published as sizeof(T) / 4 tagged words at p.
+template <class T>
+__device__ __forceinline__ void put_tagged(u64* p, unsigned gen, T val) {
+  constexpr int kW = sizeof(T) / 4;
+  unsigned u[kW];
+  memcpy(u, &val, sizeof(T));
+#pragma unroll
+  for (int i = 0; i < kW; ++i) *(volatile u64*)(p + i) = ((u64)gen << 32) | u[i];
+}
+template <class T>
+__device__ __forceinline__ bool get_tagged(const u64* p, unsigned gen, int* err, long long limit, T& val) {
+  constexpr int kW = sizeof(T) / 4;
+  unsigned u[kW];
+#pragma unroll
+  for (int i = 0; i < kW; ++i) {
+    u64 w;
+    if (!wait_word(p + i, gen, err, limit, w)) return false;
+    u[i] = (unsigned)w;
+  }
+  memcpy(&val, u, sizeof(T));
+  return true;
+}
+
+// x (forward solutions) and y (backward solutions): m tagged values each.
 // Thread (rr, ph) of the CTA handles row rr of a tile and its columns
 // ph, ph + kPh, ...; the step that gates the next tile's solve has its
 // factor block and tile inverse loaded into registers before the wait for
 // the previous tile, so only arithmetic and two block syncs remain on the
 // serial path; the other tiles are updated kGroup at a time (all of their
-// loads issued before any use, for memory-level parallelism).
+// loads issued before any use, for memory-level parallelism). The CTA that
+// will gate the next step (it owns tile t + 2) updates only that tile with
+// x_t and defers the rest of x_t's updates until it has solved and published
+// t + 2, so its share of the bulk updates never delays the chain; every tile
+// still receives x_0, x_1, ... in that order.
 template <class T>
 __global__ void __launch_bounds__(kThreads)
 k_lu_solve_flags(const T* __restrict__ A, int64_t m, const int* __restrict__ perm, const T* __restrict__ tinv,
-                 const double* __restrict__ v, T* __restrict__ work, double* __restrict__ out,
-                 unsigned* __restrict__ flags, unsigned gen, int* __restrict__ err, long long limit,
-                 const int* __restrict__ done) {
+                 const double* __restrict__ v, u64* __restrict__ work, double* __restrict__ out, unsigned gen,
+                 int* __restrict__ err, long long limit, const int* __restrict__ done) {
   count_launch();
   if (done && *done) return;
+  constexpr int kW = sizeof(T) / 4;  // tagged words per value
   extern __shared__ unsigned char smem_raw[];
   T* acc = reinterpret_cast<T*>(smem_raw);  // [my tiles][kTs]
-  __shared__ T sz[kTs];
+  __shared__ T szb[2][kTs];  // x_t (or y_t) in slot t & 1: the current column and a deferred one
   __shared__ T red[kGroup][kPh][kTs];
+  __shared__ int s_fail;
   const int64_t nt = (m + kTs - 1) / kTs;
   const int G = gridDim.x, me = blockIdx.x;
   const int mine = (int)((nt - me + G - 1) / G);  // tiles me, me + G, ...
@@ -82,8 +110,8 @@ k_lu_solve_flags(const T* __restrict__ A, int64_t m, const int* __restrict__ per
   const int rr = threadIdx.x & (kTs - 1), ph = threadIdx.x / kTs;
   const T* invL = tinv;
   const T* invU = tinv + nt * kTs * kTs;
-  T* x = work;
-  T* y = work + m;
+  u64* x = work;           // forward solutions, tagged
+  u64* y = work + m * kW;  // backward solutions, tagged
   constexpr int kPer = kTs / kPh;  // columns per thread
 
   // acc_u = (P v)_u
@@ -91,6 +119,7 @@ k_lu_solve_flags(const T* __restrict__ A, int64_t m, const int* __restrict__ per
     const int64_t row = (int64_t)(me + (e / kTs) * G) * kTs + (e % kTs);
     acc[e] = row < m ? (T)v[perm[row]] : (T)0;
   }
+  if (threadIdx.x == 0) s_fail = 0;
   __syncthreads();
 
   // this thread's values of the block A[u tile rows, t tile columns]
@@ -111,11 +140,11 @@ k_lu_solve_flags(const T* __restrict__ A, int64_t m, const int* __restrict__ per
 #pragma unroll
     for (int j = 0; j < kPer; ++j) r[j] = X[(ph + kPh * j) * kTs + rr];
   };
-  // a -= block sz
-  auto apply_block = [&](const T (&r)[kPer], T* a) {
+  // a -= block z
+  auto apply_block = [&](const T (&r)[kPer], T* a, const T* z) {
     T s = 0;
 #pragma unroll
-    for (int j = 0; j < kPer; ++j) s += r[j] * sz[ph + kPh * j];
+    for (int j = 0; j < kPer; ++j) s += r[j] * z[ph + kPh * j];
     red[0][ph][rr] = s;
     __syncthreads();
     if (ph == 0) {
@@ -126,8 +155,8 @@ k_lu_solve_flags(const T* __restrict__ A, int64_t m, const int* __restrict__ per
     }
     __syncthreads();
   };
-  // a = inv a, also written to dst (global) for the other CTAs
-  auto solve_block = [&](int64_t t, const T (&r)[kPer], T* a, T* dst) {
+  // a = inv a, also published (tagged) in dst for the other CTAs
+  auto solve_block = [&](int64_t t, const T (&r)[kPer], T* a, u64* dst) {
     T s = 0;
 #pragma unroll
     for (int j = 0; j < kPer; ++j) s += r[j] * a[ph + kPh * j];
@@ -138,16 +167,13 @@ k_lu_solve_flags(const T* __restrict__ A, int64_t m, const int* __restrict__ per
 #pragma unroll
       for (int q = 0; q < kPh; ++q) val += red[0][q][rr];
       a[rr] = val;
-      if (t * kTs + rr < m) {
-        dst[t * kTs + rr] = val;
-        __threadfence();
-      }
+      if (t * kTs + rr < m) put_tagged(dst + (t * kTs + rr) * kW, gen, val);
     }
     __syncthreads();
   };
-  // a_u -= A[u, t] sz for `count` of this CTA's tiles u0, u0 + step, ...
+  // a_u -= A[u, t] z for `count` of this CTA's tiles u0, u0 + step, ...
   constexpr int kG = sizeof(T) == 4 ? kGroup : 1;  // FP64 blocks: one at a time (registers)
-  auto update_many = [&](int64_t u0, int64_t step, int64_t count, int64_t t) {
+  auto update_many = [&](int64_t u0, int64_t step, int64_t count, int64_t t, const T* z) {
     for (int64_t g0 = 0; g0 < count; g0 += kG) {
       const int n = (int)imin64(kG, count - g0);
       T r[kG][kPer];
@@ -159,7 +185,7 @@ k_lu_solve_flags(const T* __restrict__ A, int64_t m, const int* __restrict__ per
         if (q < n) {
           T s = 0;
 #pragma unroll
-          for (int j = 0; j < kPer; ++j) s += r[q][j] * sz[ph + kPh * j];
+          for (int j = 0; j < kPer; ++j) s += r[q][j] * z[ph + kPh * j];
           red[q][ph][rr] = s;
         }
       __syncthreads();
@@ -172,19 +198,30 @@ k_lu_solve_flags(const T* __restrict__ A, int64_t m, const int* __restrict__ per
       __syncthreads();
     }
   };
-  auto publish = [&](unsigned* f) {
-    if (threadIdx.x == 0) {
-      __threadfence();
-      atomicExch(f, gen);
-    }
-  };
   // sz = the solution of tile t: this CTA's own copy, or the published one
-  auto fetch = [&](int64_t t, const T* src) {
-    if (threadIdx.x < kTs) {
-      if (t % G == me) sz[threadIdx.x] = acc[(t / G) * kTs + threadIdx.x];
-      else sz[threadIdx.x] = t * kTs + threadIdx.x < m ? __ldcg(src + t * kTs + threadIdx.x) : (T)0;
+  // (waiting for its words to carry this launch's generation; `all`: every
+  // thread polls its word at once, else thread 0 polls the tile's first
+  // word before the others read theirs); false if a wait gave up
+  auto fetch = [&](int64_t t, const u64* src, bool all, T* sz) -> bool {
+    if (t % G == me) {
+      if (threadIdx.x < kTs) sz[threadIdx.x] = acc[(t / G) * kTs + threadIdx.x];
+    } else {
+      if (!all) {
+        if (threadIdx.x == 0) {
+          u64 w;
+          if (!wait_word(src + t * kTs * kW, gen, err, limit, w)) s_fail = 1;
+        }
+        __syncthreads();
+      }
+      if (threadIdx.x < kTs && !s_fail) {
+        T val = (T)0;
+        if (t * kTs + threadIdx.x < m && !get_tagged(src + (t * kTs + threadIdx.x) * kW, gen, err, limit, val))
+          s_fail = 1;
+        sz[threadIdx.x] = val;
+      }
     }
     __syncthreads();
+    return !s_fail;
   };
 
   T pa[kPer], pinv[kPer];
@@ -192,53 +229,72 @@ k_lu_solve_flags(const T* __restrict__ A, int64_t m, const int* __restrict__ per
   if (me == 0) {
     load_inv(0, invL, pinv);
     solve_block(0, pinv, acc, x);
-    publish(flags);
   }
+  int deferred = -1;  // a column whose updates of this CTA's later tiles wait (tile counts fit an int)
   for (int64_t t = 0; t < last; ++t) {  // beyond `last` this CTA has no tile to update
     const int64_t nxt = t + 1;
+    T* zt = szb[t & 1];
     int64_t u = nxt + ((me - nxt) % G + G) % G;  // this CTA's first tile after t
     const bool gate = u == nxt;                  // it gates the next step
     if (gate) {
       load_block(nxt, t, pa);
       load_inv(nxt, invL, pinv);
     }
-    if (t % G != me && !wait_flag(flags + t, gen, err, limit)) return;
-    fetch(t, x);
+    if (!fetch(t, x, gate, zt)) return;
     if (gate) {
       T* a = acc + (nxt / G) * kTs;
-      apply_block(pa, a);
+      apply_block(pa, a, zt);
       solve_block(nxt, pinv, a, x);
-      publish(flags + nxt);
       u += G;
     }
-    if (u < nt) update_many(u, G, (nt - 1 - u) / G + 1, t);
+    if (deferred >= 0) {  // (tile t + 1 received it before)
+      if (u < nt) update_many(u, G, (nt - 1 - u) / G + 1, deferred, szb[deferred & 1]);
+      deferred = -1;
+    }
+    if (u < nt) {
+      if (!gate && u == t + 2) {  // this CTA gates the next step: that tile first, the rest after it
+        update_many(u, G, 1, t, zt);
+        deferred = (int)t;
+      } else {
+        update_many(u, G, (nt - 1 - u) / G + 1, t, zt);
+      }
+    }
   }
 
   // backward sweep: U (upper, with its diagonal) from the forward solution in acc
-  unsigned* bflags = flags + nt;
   if (last == nt - 1) {
     load_inv(nt - 1, invU, pinv);
     solve_block(nt - 1, pinv, acc + ((nt - 1) / G) * kTs, y);
-    publish(bflags + nt - 1);
   }
+  deferred = -1;
   for (int64_t t = nt - 1; t > me; --t) {  // at or below `me` this CTA has no tile to update
     const int64_t prv = t - 1;
+    T* zt = szb[t & 1];
     int64_t u = prv - ((prv - me) % G + G) % G;  // this CTA's last tile before t
     const bool gate = u == prv;
     if (gate) {
       load_block(prv, t, pa);
       load_inv(prv, invU, pinv);
     }
-    if (t % G != me && !wait_flag(bflags + t, gen, err, limit)) return;
-    fetch(t, y);
+    if (!fetch(t, y, gate, zt)) return;
     if (gate) {
       T* a = acc + (prv / G) * kTs;
-      apply_block(pa, a);
+      apply_block(pa, a, zt);
       solve_block(prv, pinv, a, y);
-      publish(bflags + prv);
       u -= G;
     }
-    if (u >= 0) update_many(u, -(int64_t)G, (u - me) / G + 1, t);
+    if (deferred >= 0) {
+      if (u >= 0) update_many(u, -(int64_t)G, (u - me) / G + 1, deferred, szb[deferred & 1]);
+      deferred = -1;
+    }
+    if (u >= 0) {
+      if (!gate && u == t - 2) {
+        update_many(u, -(int64_t)G, 1, t, zt);
+        deferred = (int)t;
+      } else {
+        update_many(u, -(int64_t)G, (u - me) / G + 1, t, zt);
+      }
+    }
   }
   for (int e = threadIdx.x; e < mine * kTs; e += kThreads) {
     const int64_t row = (int64_t)(me + (e / kTs) * G) * kTs + (e % kTs);
@@ -297,11 +353,16 @@ void lu_tile_inverses(cudaStream_t s, const T* A, int64_t m, T* tinv) {
   STOKES_LAUNCHED();
 }
 
+int64_t lu_solve_work_words(int64_t m, int elem_bytes) { return 2 * m * (elem_bytes / 4); }
+
 // z (block rows) = factors^-1 v for one block. T = double uses the FP64
-// factors, T = float a float copy of them; work: 2 m elements of T.
+// factors, T = float a float copy of them; work: lu_solve_work_words(m,
+// sizeof(T)) words with their own generation counter gen, which the caller
+// sets to 0 when it zeroes the buffer (a word is current only when its
+// generation matches the launch's, and generations start at 1).
 template <class T>
 void lu_solve_persistent(Geom& g, const T* A, int64_t m, const int* perm, const T* tinv, const double* v, double* z,
-                         T* work, const int* done) {
+                         unsigned long long* work, unsigned& gen_counter, const int* done) {
   static int grid = 0;
   const int64_t nt = (m + kTs - 1) / kTs;
   BlockDiag& b = g.bd;
@@ -320,21 +381,15 @@ void lu_solve_persistent(Geom& g, const T* A, int64_t m, const int* perm, const 
     b.barrier.alloc(4);
     STOKES_CUDA(cudaMemsetAsync(b.barrier.get(), 0, 4 * sizeof(unsigned), g.stream));
   }
-  if (b.trsv_flags.n < (size_t)(2 * nt)) {
-    b.trsv_flags.alloc(2 * nt);
-    STOKES_CUDA(cudaMemsetAsync(b.trsv_flags.get(), 0, 2 * nt * sizeof(unsigned), g.stream));
-    b.trsv_gen = 0;
+  unsigned gen = ++gen_counter;
+  if (gen == 0) {  // wrapped: clear the buffer so that no stale generation matches
+    STOKES_CUDA(cudaMemsetAsync(work, 0, lu_solve_work_words(m, sizeof(T)) * sizeof(unsigned long long), g.stream));
+    gen = gen_counter = 1;
   }
-  unsigned gen = ++b.trsv_gen;
-  if (gen == 0) {  // wrapped: clear the flags so that no stale generation matches
-    STOKES_CUDA(cudaMemsetAsync(b.trsv_flags.get(), 0, b.trsv_flags.n * sizeof(unsigned), g.stream));
-    gen = b.trsv_gen = 1;
-  }
-  unsigned* flags = b.trsv_flags.get();
   int* err = (int*)(b.barrier.get() + 2);
   long long limit = gsync::spin_limit();
-  void* args[] = {(void*)&A, (void*)&m, (void*)&perm, (void*)&tinv, (void*)&v, (void*)&work, (void*)&z,
-                  (void*)&flags, (void*)&gen, (void*)&err, (void*)&limit, (void*)&done};
+  void* args[] = {(void*)&A,   (void*)&m,   (void*)&perm, (void*)&tinv,  (void*)&v,    (void*)&work,
+                  (void*)&z,   (void*)&gen, (void*)&err,  (void*)&limit, (void*)&done};
   STOKES_CUDA(cudaLaunchCooperativeKernel((const void*)k_lu_solve_flags<T>, dim3(grid), dim3(kThreads), args, smem,
                                           g.stream));
 }
@@ -351,9 +406,9 @@ void bd_check_barrier(Geom& g) {
 template void lu_tile_inverses<double>(cudaStream_t, const double*, int64_t, double*);
 template void lu_tile_inverses<float>(cudaStream_t, const float*, int64_t, float*);
 template void lu_solve_persistent<double>(Geom&, const double*, int64_t, const int*, const double*, const double*,
-                                          double*, double*, const int*);
+                                          double*, unsigned long long*, unsigned&, const int*);
 template void lu_solve_persistent<float>(Geom&, const float*, int64_t, const int*, const float*, const double*,
-                                         double*, float*, const int*);
+                                         double*, unsigned long long*, unsigned&, const int*);
 
 unsigned long long launches_bd_trsv() { return tu_launches(); }
 

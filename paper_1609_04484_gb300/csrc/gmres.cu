@@ -23,6 +23,8 @@ namespace {
 
 constexpr int kChunk = 2048;  // vector elements per CTA in the reductions
 constexpr int kMaxRestart = 8192;
+constexpr double kF32Refine = 1e4;   // residual reduction a double-float cycle may leave to the FP32 operator
+constexpr double kDfResMargin = 0.3;  // target of a cycle started from a double-float residual, in units of tol
 
 // partial[b * ldp + k] = sum_{i in chunk b} V[k][i] w[i], k < ncols
 __global__ void __launch_bounds__(256)
@@ -356,15 +358,12 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
   const double xnorm0 = device_norm(g, x, n);
   bool x_is_zero = xnorm0 == 0.0;
   int iters = 0;
-  while (true) {
-    // true residual r = f - A x
+  // r = f - A x with the operator of precision p (x = 0: r = f); |r|
+  auto residual = [&](int p) {
     if (x_is_zero) {
       k_residual_norm<<<nblk, 256, 0, s>>>(f, nullptr, k.r.get(), n, normpart);
     } else {
-      // the true residual of the double-float solve is taken with the native
-      // FP64 operator: large densities (ill-conditioned systems) amplify the
-      // double-float operator's ~1e-12 relative error past the tolerance
-      apply_operator(g, x, k.t.get(), (precision == STOKES_DF64 && !inner) ? STOKES_FP64 : precision, nullptr);
+      apply_operator(g, x, k.t.get(), p, nullptr);
       k_residual_norm<<<nblk, 256, 0, s>>>(f, k.t.get(), k.r.get(), n, normpart);
     }
     k_norm_final<<<1, 32, 0, s>>>(normpart, nblk, k.scal.get(), 2);
@@ -372,6 +371,35 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
     double rn = 0.0;
     STOKES_CUDA(cudaMemcpyAsync(&rn, k.scal.get() + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
     STOKES_CUDA(cudaStreamSynchronize(s));
+    return rn;
+  };
+  // Double-float solves (right preconditioner): the residual a restart
+  // starts from is taken with the double-float operator, whose error
+  // (~1e-12 of the sum of the terms' magnitudes, amplified by large
+  // densities) is small against a residual well above the tolerance;
+  // convergence is decided by the native FP64 operator only, which
+  // recomputes the residual whenever the double-float one is at the
+  // tolerance or stopped falling (from then on every restart uses FP64).
+  // A cycle that starts from a double-float residual aims kDfResMargin
+  // below the tolerance, to cover that residual's error.
+  bool df_res = precision == STOKES_DF64 && !inner && !left;
+  double df_prev = -1.0;
+  bool from_df = false;
+  while (true) {
+    // true residual r = f - A x
+    const int rprec = (precision == STOKES_DF64 && !inner) ? (df_res ? STOKES_DF64 : STOKES_FP64) : precision;
+    double rn = residual(rprec);
+    from_df = false;
+    if (rprec == STOKES_DF64 && !x_is_zero) {
+      const double rel = rn / fnorm;
+      if (rel <= tol || (df_prev > 0.0 && rel > 0.5 * df_prev) || iters >= max_iter || !std::isfinite(rel)) {
+        df_res = false;
+        rn = residual(STOKES_FP64);
+      } else {
+        from_df = true;
+        df_prev = rel;
+      }
+    }
     res.relres = rn / fnorm;
     double beta = rn;
     if (left) {
@@ -396,6 +424,14 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
     k_scale<<<gv, 256, 0, s>>>(k.r.get(), k.scal.get(), 3, k.V.get(), n, nullptr);
     k_cycle_start<<<1, 256, 0, s>>>(k.g.get(), m, k.scal.get(), 2, state);
     STOKES_LAUNCHED();
+    // A double-float cycle that starts within kF32Refine tol of the tolerance
+    // only has to reduce the residual by at most kF32Refine: a refinement
+    // step, which the FP32 operator does at a seventh of the cost; the
+    // FP64 residual decides convergence.
+    const int op_prec =
+        (precision == STOKES_DF64 && !inner && !left && !x_is_zero && res.relres <= kF32Refine * tol) ? STOKES_FP32
+                                                                                                      : precision;
+    const double ctol = from_df ? kDfResMargin * tol : tol;
     const int mc = std::min(m, max_iter - iters);
     std::vector<size_t> iter_first(mc + 1, g.prof.entries.size());
     for (int j = 0; j < mc; ++j) {
@@ -403,14 +439,14 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
       double* vj = k.V.get() + (int64_t)j * n;
       double* vnext = k.V.get() + (int64_t)(j + 1) * n;  // k.w normalised into it
       if (!use_pc) {
-        apply_operator(g, vj, k.w.get(), precision, state);
+        apply_operator(g, vj, k.w.get(), op_prec, state);
       } else if (!left) {
         // flexible GMRES: keep z_j = P^-1 v_j, the iterate is x0 + Z y
         double* zj = k.Zb.get() + (int64_t)j * n;
         precond_apply(g, vj, zj, state, bd32);
-        apply_operator(g, zj, k.w.get(), precision, state);
+        apply_operator(g, zj, k.w.get(), op_prec, state);
       } else {
-        apply_operator(g, vj, k.t.get(), precision, state);
+        apply_operator(g, vj, k.t.get(), op_prec, state);
         precond_apply(g, k.t.get(), k.w.get(), state, bd32);
       }
       const int pa = g.prof.begin(kProfArnoldi, 8.0 * n * (4.0 * (j + 1) + 4.0), s);
@@ -422,7 +458,7 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
                                            pass ? np2.get() : nullptr, state);
       }
       k_arnoldi_finish<<<1, 32, 0, s>>>(j, m, np2.get(), nblk, k.H.get(), k.cs.get(), k.sn.get(), k.g.get(),
-                                        k.scal.get(), state, rhsnorm, tol);
+                                        k.scal.get(), state, rhsnorm, ctol);
       k_scale<<<gv, 256, 0, s>>>(k.w.get(), k.scal.get(), 0, vnext, n, state);
       g.prof.end(pa, s);
       STOKES_LAUNCHED();
@@ -464,8 +500,11 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
     iters += hstate[1];
     x_is_zero = false;
     if (std::getenv("STOKES_TRACE"))
-      std::fprintf(stderr, "[stokes]   cycle: %d columns, converged flag %d, breakdown %d, relres at start %.3e\n",
-                   hstate[1], hstate[0], hstate[2], res.relres);
+      std::fprintf(stderr,
+                   "[stokes]   cycle: %d columns, converged flag %d, breakdown %d, relres at start %.3e (%s), "
+                   "operator %s\n",
+                   hstate[1], hstate[0], hstate[2], res.relres, from_df ? "df64 residual" : "true residual",
+                   op_prec == STOKES_FP32 ? "fp32" : (op_prec == STOKES_DF64 ? "df64" : "fp64"));
     if (inner && hstate[0] && !hstate[2]) {
       res.iters = iters;
       res.relres = res.pc_relres = -1.0;  // not evaluated

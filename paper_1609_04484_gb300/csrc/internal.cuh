@@ -97,15 +97,13 @@ struct BlockDiag {
   DevBuf<float> inv32;            // inverses (same offsets as lu)
   DevBuf<float> lu32;             // factors of the triangular-solve blocks, packed
   std::vector<int64_t> lu32_off;  // per component offset into lu32 (-1 if none)
-  DevBuf<float> work32;           // persistent solve work vector
   DevBuf<int> d_tri_ids;          // blocks applied by triangular solves in FP64
   int64_t max_tri_rows = 0;
-  DevBuf<double> work64;
+  DevBuf<unsigned long long> trsv_work;  // tagged solutions of the persistent triangular solves
   DevBuf<double> tinv64;          // diagonal-tile inverses of the FP64 triangular-solve blocks
   std::vector<int64_t> tinv_off;  // per component offset into tinv64 (-1 if none)
   DevBuf<unsigned> barrier;       // count, generation, sticky error
-  DevBuf<unsigned> trsv_flags;    // per-tile ready flags of the persistent triangular solves
-  unsigned trsv_gen = 0;          // generation number of the last such launch
+  unsigned trsv_gen = 0;          // generation of the last solve tagged in trsv_work (0: buffer zeroed)
 };
 
 // Workspace of the Krylov solver.
@@ -200,7 +198,8 @@ struct TwoGrid {
   bool use_lu = false;             // coarse solve by the LU factors (else the explicit inverse)
   DevBuf<unsigned> barrier;        // grid barrier of the cooperative panel factorisation
   int64_t max_chunks = 0;
-  DevBuf<float> work32;
+  DevBuf<unsigned long long> trsv_work;  // tagged solutions of the coarse triangular solves
+  unsigned trsv_gen = 0;                 // generation of the last solve tagged in trsv_work (0: buffer zeroed)
   DevBuf<float> tinv;              // diagonal-tile inverses of the coarse LU factors
   DevBuf<int> d_pore_ids;
 };
@@ -361,10 +360,14 @@ int64_t tc_trailing_work_floats(int64_t m);
 int64_t lu_tile_inverse_elems(int64_t m);
 template <class T>
 void lu_tile_inverses(cudaStream_t s, const T* A, int64_t m, T* tinv);
-// z = U^-1 L^-1 P v by the persistent flag-synchronised solve; work: 2 m elements
+// 64-bit words of the work buffer of lu_solve_persistent for m rows of elem_bytes values
+int64_t lu_solve_work_words(int64_t m, int elem_bytes);
+// z = U^-1 L^-1 P v by the persistent solve that publishes tile solutions as
+// generation-tagged words; work: lu_solve_work_words(m, sizeof(T)) words and gen
+// its generation counter (0 when the buffer was zeroed)
 template <class T>
 void lu_solve_persistent(Geom& g, const T* A, int64_t m, const int* perm, const T* tinv, const double* v, double* z,
-                         T* work, const int* done);
+                         unsigned long long* work, unsigned& gen, const int* done);
 
 // ---- coarse.cu ----
 // z = Z c + B^-1 (r - Y c), c = C Z^T W r (needs cl.ready and the block diagonal)

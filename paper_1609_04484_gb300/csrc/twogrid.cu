@@ -14,6 +14,7 @@
 // The coarse solve rounds its input to float, so the solver runs flexible
 // GMRES, which tolerates a preconditioner that is not exactly linear.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -814,23 +815,38 @@ k_prolong(int64_t N, int outer, const int* __restrict__ comp, const int64_t* __r
 // from the closed form of the band-limited (periodic sinc) interpolant:
 //   S(d) = sin(nc d / 2) cot(d / 2) / nc   (nc even),
 //   S(d) = sin(nc d / 2) / (nc sin(d / 2)) (nc odd),  S(0) = 1.
-std::vector<float> trig_interp(int64_t nc, int64_t nf) {
-  std::vector<float> P((size_t)(nf * nc));
-  for (int64_t i = 0; i < nf; ++i)
-    for (int64_t j = 0; j < nc; ++j) {
-      const double d = 2.0 * kPi * (double)i / (double)nf - 2.0 * kPi * (double)j / (double)nc;
-      const double sh = std::sin(0.5 * d);
-      double v;
-      if (std::fabs(sh) < 1e-12) {
-        v = 1.0;  // d is a multiple of 2 pi: the sample itself
-      } else if (nc % 2 == 0) {
-        v = std::sin(0.5 * (double)nc * d) * std::cos(0.5 * d) / (sh * (double)nc);
-      } else {
-        v = std::sin(0.5 * (double)nc * d) / (sh * (double)nc);
-      }
-      P[(size_t)(i * nc + j)] = (float)v;
+// Weight of coarse sample j at fine node i of the trigonometric interpolant
+// from nc to nf = q nc equispaced samples: a function of the angle
+// d = 2 pi (i / nf - j / nc) = 2 pi delta / nf, delta = (i - q j) mod nf
+// (the weight is 2 pi-periodic in d), so one row of nf values, V[delta],
+// gives the whole nf x nc matrix.
+std::vector<float> trig_interp_row(int64_t nc, int64_t nf) {
+  std::vector<float> V((size_t)nf);
+  for (int64_t delta = 0; delta < nf; ++delta) {
+    const double d = 2.0 * kPi * (double)delta / (double)nf;
+    const double sh = std::sin(0.5 * d);
+    double v;
+    if (delta == 0) {
+      v = 1.0;  // the sample itself
+    } else if (nc % 2 == 0) {
+      v = std::sin(0.5 * (double)nc * d) * std::cos(0.5 * d) / (sh * (double)nc);
+    } else {
+      v = std::sin(0.5 * (double)nc * d) / (sh * (double)nc);
     }
-  return P;
+    V[(size_t)delta] = (float)v;
+  }
+  return V;
+}
+
+// P[i][j] = V[(i - q j) mod nf] for the row-major nf x nc matrix P.
+__global__ void k_fill_interp(const float* __restrict__ V, int64_t nf, int64_t nc, int q, float* __restrict__ P) {
+  count_launch();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nf * nc; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / nc, j = e - i * nc;
+    int64_t d = (i - (int64_t)q * j) % nf;
+    if (d < 0) d += nf;
+    P[e] = V[d];
+  }
 }
 
 }  // namespace
@@ -871,27 +887,38 @@ void twogrid_setup(Geom& g, int q, int coarse_mode) {
   t.Nc = Nc;
   const int64_t m = 2 * Nc;
   require((double)m * (double)m * 4.0 < 64e9, "two-grid: coarse operator too large (reduce with a larger q)");
-  // interpolation matrices, one per distinct (n_f, n_c)
+  // interpolation matrices, one per distinct (n_f, n_c), filled on the GPU
+  // from one row of weights each
   std::map<std::pair<int64_t, int64_t>, int64_t> seen;
-  std::vector<float> pool;
+  std::vector<float> vpool;
+  std::vector<std::array<int64_t, 4>> fills;  // n_f, n_c, offset of P, offset of its row V
+  int64_t ptotal = 0;
   std::vector<int64_t> ioff(nc);
   for (int k = 0; k < nc; ++k) {
     const int64_t nf = g.off[k + 1] - g.off[k], ncc = nf / q;
     auto key = std::make_pair(nf, ncc);
     auto it = seen.find(key);
     if (it == seen.end()) {
-      const std::vector<float> P = trig_interp(ncc, nf);
-      seen[key] = (int64_t)pool.size();
-      ioff[k] = (int64_t)pool.size();
-      pool.insert(pool.end(), P.begin(), P.end());
+      const std::vector<float> V = trig_interp_row(ncc, nf);
+      seen[key] = ptotal;
+      ioff[k] = ptotal;
+      fills.push_back({nf, ncc, ptotal, (int64_t)vpool.size()});
+      vpool.insert(vpool.end(), V.begin(), V.end());
+      ptotal += nf * ncc;
     } else {
       ioff[k] = it->second;
     }
   }
-  t.interp.alloc(pool.size());
+  t.interp.alloc(ptotal);
   t.d_ioff.alloc(nc);
   t.d_off_c.alloc(nc + 1);
-  STOKES_CUDA(cudaMemcpyAsync(t.interp.get(), pool.data(), 4 * pool.size(), cudaMemcpyHostToDevice, s));
+  DevBuf<float> vrows;  // freed at the end of the setup, after its uses
+  vrows.alloc(vpool.size());
+  STOKES_CUDA(cudaMemcpyAsync(vrows.get(), vpool.data(), 4 * vpool.size(), cudaMemcpyHostToDevice, s));
+  for (const auto& fl : fills)
+    k_fill_interp<<<(unsigned)std::min<int64_t>((fl[0] * fl[1] + 255) / 256, 152 * 16), 256, 0, s>>>(
+        vrows.get() + fl[3], fl[0], fl[1], q, t.interp.get() + fl[2]);
+  STOKES_LAUNCHED();
   STOKES_CUDA(cudaMemcpyAsync(t.d_ioff.get(), ioff.data(), 8 * nc, cudaMemcpyHostToDevice, s));
   STOKES_CUDA(cudaMemcpyAsync(t.d_off_c.get(), t.off_c.data(), 8 * (nc + 1), cudaMemcpyHostToDevice, s));
   // coarse nodes
@@ -1119,7 +1146,9 @@ void twogrid_setup(Geom& g, int q, int coarse_mode) {
   t.use_lu = coarse_mode == STOKES_TG_COARSE_LU || (coarse_mode == STOKES_TG_COARSE_AUTO && m > kMaxExplicitCoarse);
   if (t.use_lu) {
     t.inv.release();
-    t.work32.alloc(2 * m);
+    t.trsv_work.alloc(lu_solve_work_words(m, sizeof(float)));
+    STOKES_CUDA(cudaMemsetAsync(t.trsv_work.get(), 0, lu_solve_work_words(m, sizeof(float)) * 8, s));
+    t.trsv_gen = 0;
     t.tinv.alloc(lu_tile_inverse_elems(m));
     lu_tile_inverses<float>(s, t.lu.get(), m, t.tinv.get());
   } else {
@@ -1148,8 +1177,8 @@ static void twogrid_apply(Geom& g, const double* r, double* z, const int* done, 
   const int64_t m = 2 * t.Nc;
   const int pc = g.prof.begin(kProfCoarseSolve, 4.0 * (double)m * (double)m, s);
   if (t.use_lu) {
-    lu_solve_persistent<float>(g, t.lu.get(), m, t.perm.get(), t.tinv.get(), t.rc.get(), t.zc.get(), t.work32.get(),
-                               done);
+    lu_solve_persistent<float>(g, t.lu.get(), m, t.perm.get(), t.tinv.get(), t.rc.get(), t.zc.get(),
+                               t.trsv_work.get(), t.trsv_gen, done);
   } else {
     k_dense_gemv32_part<<<dim3((unsigned)((m + 1023) / 1024), kGemvSplits), 256, 0, s>>>(
         t.inv.get(), m, t.rc32.get(), t.gemv_part.get(), done);

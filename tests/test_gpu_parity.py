@@ -326,14 +326,18 @@ def test_profile_records_pair_launches(S, dev):
         sig = np.zeros_like(f)
         code, iters, rr, _ = S.stokes_gmres_solve(G.handle, f, sig, tol=1e-10, restart=30, precision=S.STOKES_DF64)
         n, ms, units = S.stokes_profile_read(G.handle, S.STOKES_PROF_PAIRS_DF64)
+        n32 = S.stokes_profile_read(G.handle, S.STOKES_PROF_PAIRS_FP32)[0]
+        n64 = S.stokes_profile_read(G.handle, S.STOKES_PROF_PAIRS_FP64)[0]
         cycles = -(-iters // 30)
-        # one double-float pair launch per iteration; the true residual after
-        # each cycle uses the FP64 kernel; flexible GMRES applies the
-        # preconditioner once per iteration
-        assert n == iters
+        # one pair launch per iteration (double-float, or FP32 in a cycle that
+        # starts within 1e4 tol of the tolerance); one double-float launch for
+        # the residual each restart starts from; the FP64 kernel only confirms
+        # convergence (at least once, at most once per restart); flexible
+        # GMRES applies the preconditioner once per iteration
+        assert iters + cycles <= n + n32 <= iters + cycles + 2
+        assert 1 <= n64 <= cycles
         assert units == pytest.approx(n * g.n_nodes**2)
         assert ms > 0
-        assert S.stokes_profile_read(G.handle, S.STOKES_PROF_PAIRS_FP64)[0] == cycles
         nb, msb, ub = S.stokes_profile_read(G.handle, S.STOKES_PROF_BD_APPLY)
         assert nb == iters and msb > 0
         S.stokes_profile_enable(G.handle, False)
