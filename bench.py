@@ -52,10 +52,11 @@ LU_PANEL_TC = 128  # panel width of the coarse LU with tensor-core trailing upda
 MEASURED_TRAFFIC = {("k_dlp_pairs_df64", 256, 1, 256): 9828608.0,
                     ("k_dlp_pairs_f32", 256, 4, 256): 7642624.0}
 # DRAM bytes per algorithmic byte of a kernel whose launches differ in size,
-# from one ncu capture on a smaller case (k_tc_trailing: the 11,392-row update
-# of an 11,776-row coarse LU, 1003.9 MB against 8 rest^2 = 1038.2 MB); the
-# traffic of a launch of the large workload is this ratio times its bytes
-MEASURED_TRAFFIC_RATIO = {"k_tc_trailing": 0.967}
+# from ncu captures of launches of this workload (k_tc_trailing: the first
+# trailing updates of the 136,192-node step); the traffic of an average
+# launch is this ratio times its algorithmic bytes. Empty: not captured as the
+# kernel now stands
+MEASURED_TRAFFIC_RATIO = {"k_tc_trailing": 1.07}
 
 
 def parse_args():
@@ -714,14 +715,14 @@ def main():
     dom = max(rooflines, key=lambda r: r["ms_per_step"] if r["candidate"] else -1.0)
     roofline = dict(dom)
     roofline.pop("candidate", None)
-    traffic = None
-    if args.workload == "pipe1000":
+    traffic, source = dom.get("traffic"), dom.get("traffic_source")
+    if traffic is None and args.workload == "pipe1000":
         key = (dom["kernel"],) + tuple(tuned.get(dom.get("precision"), {}).get("shape", ()))
         traffic = MEASURED_TRAFFIC.get(key)
+        source = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture of this kernel shape on this "
+                  "workload" if traffic else "no ncu capture of this kernel as it now stands")
     roofline["traffic"] = traffic
-    roofline["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture of this kernel "
-                                  "shape on this workload" if traffic else
-                                  "no ncu capture of this kernel as it now stands")
+    roofline["traffic_source"] = source
     phases = {}
     for k, (n, ms, units) in ((k, v) for k, v in prof_acc.items() if isinstance(k, int)):
         if n:
@@ -842,10 +843,13 @@ def kernel_rooflines(S, prof_acc, peaks):
                           "peak_source": peaks["source"],
                           "algorithmic_bytes": "8 rest^2 per launch (C read and written; the rest x 128 operands "
                                                "come from L2)",
-                          "traffic": round(MEASURED_TRAFFIC_RATIO["k_tc_trailing"] * units / (2.0 * LU_PANEL_TC) * 8.0
-                                           / max(n, 1)),
-                          "traffic_source": "ncu DRAM bytes / algorithmic bytes of one launch on the 11,776-row case "
-                                            "(0.967) times the average launch's algorithmic bytes",
+                          "traffic": (round(MEASURED_TRAFFIC_RATIO["k_tc_trailing"] * units / (2.0 * LU_PANEL_TC)
+                                            * 8.0 / max(n, 1)) if "k_tc_trailing" in MEASURED_TRAFFIC_RATIO
+                                      else None),
+                          "traffic_source": ("ncu DRAM bytes / algorithmic bytes of the first launches of this "
+                                             "workload's step, times the average launch's algorithmic bytes"
+                                             if "k_tc_trailing" in MEASURED_TRAFFIC_RATIO else
+                                             "no ncu capture of this kernel as it now stands"),
                           "tensor": {"useful_tflops": round(flops / 1e12, 2),
                                      "issued_tflops": round(3 * flops / 1e12, 2),
                                      "tf32_peak": round(tf32_peak, 1),

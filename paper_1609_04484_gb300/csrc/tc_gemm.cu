@@ -146,8 +146,10 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
+// Two adjacent 32-column slices (columns [0, 32) and [32, 64) from taddr) with
+// one wait for both loads.
+__device__ __forceinline__ void tmem_ld32x2(uint32_t taddr, float (&v0)[32], float (&v1)[32]) {
+  uint32_t r[64];
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
       "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
@@ -156,9 +158,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
         "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
         "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+        "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+        "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+        "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr + 32u));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 32; ++i) {
+    v0[i] = __uint_as_float(r[i]);
+    v1[i] = __uint_as_float(r[32 + i]);
+  }
 }
 
 __device__ __forceinline__ float to_tf32(float a) {
@@ -200,6 +213,23 @@ k_tc_prep(const float* __restrict__ A, int64_t m, int64_t k0, int kb, int64_t ba
       blo[(r0 + c) * kb + k] = a - h;
     }
   }
+}
+
+// Output tile t of the mt x mt tiles: groups of kGroupCols column strips
+// one after the other, and inside a group the column index fastest. The
+// CTAs then work on a few row tiles and up to kGroupCols column tiles at a
+// time: a row tile's operand slabs serve kGroupCols consecutive tiles from
+// L2, and the group's column slabs (kGroupCols x 128 KB) stay there for the
+// whole group, so the operands come from DRAM about once per group instead
+// of once per column strip (at 68k rows they exceed L2, and a column-strip
+// order re-read them: 1.31 x the algorithmic DRAM bytes).
+constexpr int64_t kGroupCols = 64;
+__device__ __forceinline__ void tile_of(int64_t t, int64_t mt, int64_t& tr, int64_t& tcol) {
+  const int64_t span = kGroupCols * mt;
+  const int64_t grp = t / span, within = t - grp * span;
+  const int64_t width = imin64(kGroupCols, mt - grp * kGroupCols);
+  tr = within / width;
+  tcol = grp * kGroupCols + (within - tr * width);
 }
 
 struct TcMaps {
@@ -255,7 +285,9 @@ k_tc_trailing(const __grid_constant__ TcMaps maps, float* __restrict__ C, int64_
       for (int s = 0; s < kStages; ++s) armed_round[s] = -1;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const int rm = (int)((t % mt) * kBM), rn = (int)((t / mt) * kBN);
+        int64_t tr, tcol;
+        tile_of(t, mt, tr, tcol);
+        const int rm = (int)(tr * kBM), rn = (int)(tcol * kBN);
         for (int h = 0; h < nslices && ok; ++h, ++it) {
           const int s = (int)(it % kStages);
           const uint32_t round = (uint32_t)(it / kStages);
@@ -315,12 +347,18 @@ k_tc_trailing(const __grid_constant__ TcMaps maps, float* __restrict__ C, int64_
       const uint32_t use = (uint32_t)(ti >> 1);
       if (!mbar_wait(&tfull[b], use & 1, err)) break;
       tc_fence_after();
-      const int64_t row = (t % mt) * kBM + 32 * g + lane;
-      const int64_t col0 = (t / mt) * kBN + 64 * half;
-#pragma unroll 1
-      for (int j = 0; j < 2; ++j) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * g) << 16) + (uint32_t)(b * kBN + 64 * half + 32 * j), v);
+      int64_t tr, tcol;
+      tile_of(t, mt, tr, tcol);
+      const int64_t row = tr * kBM + 32 * g + lane;
+      const int64_t col0 = tcol * kBN + 64 * half;
+      // both 32-column slices into registers, then the accumulator is free:
+      // the MMAs of tile ti + 2 need not wait for C's update below
+      float v0[32], v1[32];
+      tmem_ld32x2(tmem + ((uint32_t)(32 * g) << 16) + (uint32_t)(b * kBN + 64 * half), v0, v1);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[b]);
+      auto emit = [&](const float (&v)[32], int j) {
         if (reduce_c) {
           // a box that starts inside the trailing block may reach past it:
           // those rows and columns fall outside the map (base + rest = m)
@@ -342,17 +380,19 @@ k_tc_trailing(const __grid_constant__ TcMaps maps, float* __restrict__ C, int64_
         } else if (row < rest) {
           float* cp = C + (base + col0 + 32 * j) * ldc + base + row;
           const int ncol = (int)imin64(32, rest - (col0 + 32 * j));
-          float old[32];
 #pragma unroll
-          for (int c = 0; c < 32; ++c) old[c] = c < ncol ? cp[(int64_t)c * ldc] : 0.f;
+          for (int h = 0; h < 32; h += 16) {  // 16 columns of loads in flight, then their stores
+            float old[16];
 #pragma unroll
-          for (int c = 0; c < 32; ++c)
-            if (c < ncol) cp[(int64_t)c * ldc] = old[c] - v[c];
+            for (int c = 0; c < 16; ++c) old[c] = h + c < ncol ? cp[(int64_t)(h + c) * ldc] : 0.f;
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+              if (h + c < ncol) cp[(int64_t)(h + c) * ldc] = old[c] - v[h + c];
+          }
         }
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[b]);
+      };
+      emit(v0, 0);
+      emit(v1, 1);
     }
     if (issued && lane == 0) bulk_wait_all();  // C is complete before the CTA leaves
     __syncwarp();
