@@ -676,28 +676,42 @@ __global__ void k_laswp32(float* __restrict__ A, int64_t m, int64_t k0, int kb, 
   }
 }
 
-// U12 rows [k0, k0 + kb) (kb <= kNb) of the columns q0 <= q < q1: each
-// thread solves L11 x = A[k0 .. k0 + kb)[q] for one column by forward
-// substitution.
-__global__ void k_trsm_row_panel32(float* __restrict__ A, int64_t m, int64_t k0, int kb, int64_t q0, int64_t q1) {
+// U12 rows [k0, k0 + kb) (kb <= kNb) of the columns q0 <= q < q1: the
+// forward substitution L11 x = A[k0 .. k0 + kb)[q] per column. A CTA takes 32
+// columns: L11 and the 32 column segments are loaded into shared memory with
+// coalesced accesses (each column segment is kb contiguous floats), four
+// lanes solve one column (rows r = sub, sub + 4, ...; a warp sync per step),
+// and the results are stored back the same way. Each entry sees the same
+// operations in the same order as a column-at-a-time substitution.
+constexpr int kTrsmCols = 32;
+__global__ void __launch_bounds__(128)
+k_trsm_row_panel32(float* __restrict__ A, int64_t m, int64_t k0, int kb, int64_t q0, int64_t q1) {
   count_launch();
-  const int64_t q = q0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (q >= q1) return;
-  float* col = A + q * m + k0;
-  float x[kNb];
-#pragma unroll
-  for (int c = 0; c < kNb; ++c) x[c] = c < kb ? col[c] : 0.f;
-#pragma unroll
-  for (int c = 0; c < kNb; ++c) {
-    if (c >= kb) break;
-    const float xc = x[c];
-#pragma unroll
-    for (int r = c + 1; r < kNb; ++r)
-      if (r < kb) x[r] -= A[(k0 + c) * m + k0 + r] * xc;
+  __shared__ float sL[kNb][kNb + 1];        // [c][r] = L11[r][c]
+  __shared__ float sX[kTrsmCols][kNb + 1];  // [j][r]
+  const int64_t qb = q0 + (int64_t)blockIdx.x * kTrsmCols;
+  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+    const int c = e / kb, r = e - c * kb;
+    sL[c][r] = A[(k0 + c) * m + k0 + r];
   }
-#pragma unroll
-  for (int c = 0; c < kNb; ++c)
-    if (c < kb) col[c] = x[c];
+  for (int e = threadIdx.x; e < kTrsmCols * kb; e += blockDim.x) {
+    const int j = e / kb, r = e - j * kb;
+    const int64_t q = qb + j;
+    sX[j][r] = q < q1 ? A[q * m + k0 + r] : 0.f;
+  }
+  __syncthreads();
+  const int j = threadIdx.x >> 2, sub = threadIdx.x & 3;  // column j of the CTA, rows sub + 4 i
+  for (int c = 0; c < kb; ++c) {
+    const float xc = sX[j][c];
+    for (int r = c + 1 + ((sub - (c + 1)) & 3); r < kb; r += 4) sX[j][r] -= sL[c][r] * xc;
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kTrsmCols * kb; e += blockDim.x) {
+    const int jj = e / kb, r = e - jj * kb;
+    const int64_t q = qb + jj;
+    if (q < q1) A[q * m + k0 + r] = sX[jj][r];
+  }
 }
 
 // rc = R r per component (x and y): rc_j = (n_c / n_f) sum_i P[i][j] r_i.
@@ -1068,7 +1082,7 @@ void twogrid_setup(Geom& g, int q, int coarse_mode) {
       factor_subpanel(ks, ws);
       const int64_t q0 = ks + ws, q1 = k0 + kb;
       if (q1 > q0) {
-        k_trsm_row_panel32<<<(unsigned)((q1 - q0 + 127) / 128), 128, 0, s>>>(A, m, ks, ws, q0, q1);
+        k_trsm_row_panel32<<<(unsigned)((q1 - q0 + kTrsmCols - 1) / kTrsmCols), 128, 0, s>>>(A, m, ks, ws, q0, q1);
         sgemm32(s, m - q0, q1 - q0, ws, -1.f, A + ks * m + q0, m, A + q0 * m + ks, m, 1.f, A + q0 * m + q0, m);
       }
     }
@@ -1080,7 +1094,7 @@ void twogrid_setup(Geom& g, int q, int coarse_mode) {
       // blocks of kNb rows: solve the first block, subtract its product from
       // the rest of the panel's rows, solve the second
       const int64_t base = k0 + kb;
-      const unsigned gq = (unsigned)((rest + 127) / 128);
+      const unsigned gq = (unsigned)((rest + kTrsmCols - 1) / kTrsmCols);
       k_trsm_row_panel32<<<gq, 128, 0, s>>>(A, m, k0, std::min(kb, kNb), base, m);
       if (kb > kNb) {
         sgemm32(s, kb - kNb, rest, kNb, -1.f, A + k0 * m + k0 + kNb, m, A + base * m + k0, m, 1.f,
