@@ -35,7 +35,22 @@ namespace {
 constexpr int kTs = 64;
 constexpr int kThreads = 512;
 constexpr int kPh = kThreads / kTs;  // column phases of a tile
-constexpr int kGroup = 2;            // tiles updated per pass of update_many
+constexpr int kGroupF = 3;  // float factor blocks per group of the bulk updates (16 KB each)
+constexpr int kGroupD = 1;  // double factor blocks per group (32 KB each)
+template <class T>
+__host__ __device__ constexpr int group_blocks() { return sizeof(T) == 4 ? kGroupF : kGroupD; }
+// dynamic shared memory of the bulk updates' two group buffers
+template <class T>
+constexpr size_t update_buffer_bytes() { return 2 * (size_t)group_blocks<T>() * kTs * kTs * sizeof(T); }
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 typedef unsigned long long u64;
 
@@ -84,23 +99,29 @@ __device__ __forceinline__ bool get_tagged(const u64* p, unsigned gen, int* err,
 // factor block and tile inverse loaded into registers before the wait for
 // the previous tile, so only arithmetic and two block syncs remain on the
 // serial path; the other tiles are updated kGroup at a time (all of their
-// loads issued before any use, for memory-level parallelism). The CTA that
+// loads issued before any use, for memory-level parallelism). The bulk
+// updates read their factor blocks from shared memory: a group of blocks is
+// copied in (cp.async, 16 bytes per copy) while the previous group is used,
+// and the first group of a step's updates is requested before the wait for
+// that step's solution, since the factors do not depend on it. The CTA that
 // will gate the next step (it owns tile t + 2) updates only that tile with
 // x_t and defers the rest of x_t's updates until it has solved and published
 // t + 2, so its share of the bulk updates never delays the chain; every tile
 // still receives x_0, x_1, ... in that order.
 template <class T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 1)
 k_lu_solve_flags(const T* __restrict__ A, int64_t m, const int* __restrict__ perm, const T* __restrict__ tinv,
                  const double* __restrict__ v, u64* __restrict__ work, double* __restrict__ out, unsigned gen,
                  int* __restrict__ err, long long limit, const int* __restrict__ done) {
   count_launch();
   if (done && *done) return;
   constexpr int kW = sizeof(T) / 4;  // tagged words per value
-  extern __shared__ unsigned char smem_raw[];
-  T* acc = reinterpret_cast<T*>(smem_raw);  // [my tiles][kTs]
+  constexpr int kGa = group_blocks<T>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sbuf = reinterpret_cast<T*>(smem_raw);  // [2][kGa][kTs columns][kTs rows]: factor blocks
+  T* acc = sbuf + 2 * kGa * kTs * kTs;       // [my tiles][kTs]
   __shared__ T szb[2][kTs];  // x_t (or y_t) in slot t & 1: the current column and a deferred one
-  __shared__ T red[kGroup][kPh][kTs];
+  __shared__ T red[kGa][kPh][kTs];
   __shared__ int s_fail;
   const int64_t nt = (m + kTs - 1) / kTs;
   const int G = gridDim.x, me = blockIdx.x;
@@ -171,21 +192,69 @@ k_lu_solve_flags(const T* __restrict__ A, int64_t m, const int* __restrict__ per
     }
     __syncthreads();
   };
+  // Copies of group gi of the blocks A[u0 + i step, t], i < count, into
+  // buffer bsel, as one cp.async group per thread (possibly empty); rows and
+  // columns past m are zero-filled. With m a multiple of 16 / sizeof(T) every
+  // copy is 16-byte aligned; otherwise the group is loaded synchronously.
+  constexpr int kEpc = 16 / (int)sizeof(T);  // elements per 16-byte copy
+  constexpr int kCpc = kTs / kEpc;            // copies per column of a block
+  const bool async_ok = m % kEpc == 0;
+  auto issue_group = [&](int64_t u0, int64_t step, int64_t count, int64_t t, int gi, int bsel) {
+    const int64_t i0 = (int64_t)gi * kGa;
+    const int n = (int)imin64(kGa, count - i0);
+    T* dstb = sbuf + (size_t)bsel * kGa * kTs * kTs;
+    const int64_t c0 = t * kTs;
+    for (int e = threadIdx.x; e < n * kTs * kCpc; e += kThreads) {
+      const int q = e / (kTs * kCpc), w = e - q * (kTs * kCpc);
+      const int c = w / kCpc, r0 = (w - c * kCpc) * kEpc;
+      const int64_t row = (u0 + (i0 + q) * step) * kTs + r0, col = c0 + c;
+      T* dst = dstb + ((size_t)q * kTs + c) * kTs + r0;
+      const int valid = (col < m && row < m) ? (int)imin64(kEpc, m - row) : 0;
+      if (async_ok) {
+        cp_async16(dst, valid > 0 ? (const void*)(A + col * m + row) : (const void*)A, valid * (int)sizeof(T));
+      } else {
+#pragma unroll
+        for (int k = 0; k < kEpc; ++k) dst[k] = k < valid ? A[col * m + row + k] : (T)0;
+      }
+    }
+    cp_async_commit();
+  };
+  bool pending = false;  // group 0 of (pend_u0, pend_t) is in flight into buffer 0
+  int64_t pend_u0 = -1, pend_t = -1;
+  auto prefetch = [&](int64_t u0, int64_t step, int64_t count, int64_t t) {
+    if (count <= 0) return;
+    issue_group(u0, step, count, t, 0, 0);
+    pending = true;
+    pend_u0 = u0;
+    pend_t = t;
+  };
   // a_u -= A[u, t] z for `count` of this CTA's tiles u0, u0 + step, ...
-  constexpr int kG = sizeof(T) == 4 ? kGroup : 1;  // FP64 blocks: one at a time (registers)
   auto update_many = [&](int64_t u0, int64_t step, int64_t count, int64_t t, const T* z) {
-    for (int64_t g0 = 0; g0 < count; g0 += kG) {
-      const int n = (int)imin64(kG, count - g0);
-      T r[kG][kPer];
+    if (count <= 0) return;
+    if (pending && (pend_u0 != u0 || pend_t != t)) {  // not the prefetched updates: let it land first
+      cp_async_wait<0>();
+      __syncthreads();
+      pending = false;
+    }
+    if (!pending) issue_group(u0, step, count, t, 0, 0);
+    pending = false;
+    const int ngroups = (int)((count + kGa - 1) / kGa);
+    for (int gi = 0; gi < ngroups; ++gi) {
+      if (gi + 1 < ngroups) {
+        issue_group(u0, step, count, t, gi + 1, (gi + 1) & 1);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();
+      const int n = (int)imin64(kGa, count - (int64_t)gi * kGa);
+      const T* bufp = sbuf + (size_t)(gi & 1) * kGa * kTs * kTs;
 #pragma unroll
-      for (int q = 0; q < kG; ++q)
-        if (q < n) load_block(u0 + (g0 + q) * step, t, r[q]);
-#pragma unroll
-      for (int q = 0; q < kG; ++q)
+      for (int q = 0; q < kGa; ++q)
         if (q < n) {
           T s = 0;
 #pragma unroll
-          for (int j = 0; j < kPer; ++j) s += r[q][j] * z[ph + kPh * j];
+          for (int j = 0; j < kPer; ++j) s += bufp[((size_t)q * kTs + ph + kPh * j) * kTs + rr] * z[ph + kPh * j];
           red[q][ph][rr] = s;
         }
       __syncthreads();
@@ -193,9 +262,9 @@ k_lu_solve_flags(const T* __restrict__ A, int64_t m, const int* __restrict__ per
         T sum = 0;
 #pragma unroll
         for (int q = 0; q < kPh; ++q) sum += red[ph][q][rr];
-        acc[((u0 + (g0 + ph) * step) / G) * kTs + rr] -= sum;
+        acc[((u0 + ((int64_t)gi * kGa + ph) * step) / G) * kTs + rr] -= sum;
       }
-      __syncthreads();
+      __syncthreads();  // the buffer of group gi is free for group gi + 2
     }
   };
   // sz = the solution of tile t: this CTA's own copy, or the published one
@@ -240,7 +309,18 @@ k_lu_solve_flags(const T* __restrict__ A, int64_t m, const int* __restrict__ per
       load_block(nxt, t, pa);
       load_inv(nxt, invL, pinv);
     }
-    if (!fetch(t, x, gate, zt)) return;
+    {  // the first group of this step's first bulk update, before the wait
+      const int64_t ua = gate ? u + G : u;
+      if (ua < nt) {
+        if (deferred >= 0) prefetch(ua, G, (nt - 1 - ua) / G + 1, deferred);
+        else if (!gate && u == t + 2) prefetch(u, G, 1, t);
+        else prefetch(ua, G, (nt - 1 - ua) / G + 1, t);
+      }
+    }
+    if (!fetch(t, x, gate, zt)) {
+      cp_async_wait<0>();  // own copies in flight land before the CTA leaves
+      return;
+    }
     if (gate) {
       T* a = acc + (nxt / G) * kTs;
       apply_block(pa, a, zt);
@@ -276,7 +356,18 @@ k_lu_solve_flags(const T* __restrict__ A, int64_t m, const int* __restrict__ per
       load_block(prv, t, pa);
       load_inv(prv, invU, pinv);
     }
-    if (!fetch(t, y, gate, zt)) return;
+    {
+      const int64_t ua = gate ? u - G : u;
+      if (ua >= 0) {
+        if (deferred >= 0) prefetch(ua, -(int64_t)G, (ua - me) / G + 1, deferred);
+        else if (!gate && u == t - 2) prefetch(u, -(int64_t)G, 1, t);
+        else prefetch(ua, -(int64_t)G, (ua - me) / G + 1, t);
+      }
+    }
+    if (!fetch(t, y, gate, zt)) {
+      cp_async_wait<0>();  // own copies in flight land before the CTA leaves
+      return;
+    }
     if (gate) {
       T* a = acc + (prv / G) * kTs;
       apply_block(pa, a, zt);
@@ -372,8 +463,10 @@ void lu_solve_persistent(Geom& g, const T* A, int64_t m, const int* perm, const 
     STOKES_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     grid = nsm;  // one CTA per SM: all resident
   }
-  const size_t smem = (size_t)((nt + grid - 1) / grid) * kTs * sizeof(T);
-  require(smem <= 48 * 1024, "triangular solve: block too large for the per-CTA tile store");
+  const size_t tiles_bytes = (size_t)((nt + grid - 1) / grid) * kTs * sizeof(T);
+  require(tiles_bytes <= 64 * 1024, "triangular solve: block too large for the per-CTA tile store");
+  const size_t smem = update_buffer_bytes<T>() + tiles_bytes;
+  STOKES_CUDA(cudaFuncSetAttribute(k_lu_solve_flags<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   STOKES_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lu_solve_flags<T>, kThreads, smem));
   require(per_sm >= 1, "persistent triangular solve does not fit on an SM", STOKES_ECUDA);
