@@ -215,21 +215,20 @@ k_tc_prep(const float* __restrict__ A, int64_t m, int64_t k0, int kb, int64_t ba
   }
 }
 
-// Output tile t of the mt x mt tiles: groups of kGroupCols column strips
-// one after the other, and inside a group the column index fastest. The
-// CTAs then work on a few row tiles and up to kGroupCols column tiles at a
-// time: a row tile's operand slabs serve kGroupCols consecutive tiles from
-// L2, and the group's column slabs (kGroupCols x 128 KB) stay there for the
-// whole group, so the operands come from DRAM about once per group instead
-// of once per column strip (at 68k rows they exceed L2, and a column-strip
-// order re-read them: 1.31 x the algorithmic DRAM bytes).
-constexpr int64_t kGroupCols = 64;
-__device__ __forceinline__ void tile_of(int64_t t, int64_t mt, int64_t& tr, int64_t& tcol) {
-  const int64_t span = kGroupCols * mt;
+// Output tile t of the mt x mt tiles: groups of G row tiles (G = the grid
+// size) taken one after the other, and inside a group the row index fastest.
+// At each moment the CTAs then work on G vertically adjacent tiles of one or
+// two column strips: C is read and written in runs of G x 512 contiguous
+// bytes per column (the 512-byte segments of a single tile are 272 KB apart
+// at 68k rows, which costs DRAM page locality), every CTA keeps its row
+// tile for the whole group (its operand slabs stay in L2: G x 128 KB), and
+// one column tile's slabs serve all CTAs at once.
+__device__ __forceinline__ void tile_of(int64_t t, int64_t mt, int64_t G, int64_t& tr, int64_t& tcol) {
+  const int64_t span = G * mt;
   const int64_t grp = t / span, within = t - grp * span;
-  const int64_t width = imin64(kGroupCols, mt - grp * kGroupCols);
-  tr = within / width;
-  tcol = grp * kGroupCols + (within - tr * width);
+  const int64_t width = imin64(G, mt - grp * G);  // row tiles in this group
+  tcol = within / width;
+  tr = grp * G + (within - tcol * width);
 }
 
 struct TcMaps {
@@ -286,7 +285,7 @@ k_tc_trailing(const __grid_constant__ TcMaps maps, float* __restrict__ C, int64_
       bool ok = true;
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         int64_t tr, tcol;
-        tile_of(t, mt, tr, tcol);
+        tile_of(t, mt, gridDim.x, tr, tcol);
         const int rm = (int)(tr * kBM), rn = (int)(tcol * kBN);
         for (int h = 0; h < nslices && ok; ++h, ++it) {
           const int s = (int)(it % kStages);
@@ -348,7 +347,7 @@ k_tc_trailing(const __grid_constant__ TcMaps maps, float* __restrict__ C, int64_
       if (!mbar_wait(&tfull[b], use & 1, err)) break;
       tc_fence_after();
       int64_t tr, tcol;
-      tile_of(t, mt, tr, tcol);
+      tile_of(t, mt, gridDim.x, tr, tcol);
       const int64_t row = tr * kBM + 32 * g + lane;
       const int64_t col0 = tcol * kBN + 64 * half;
       // both 32-column slices into registers, then the accumulator is free:
