@@ -35,7 +35,7 @@ namespace {
 constexpr int kTs = 64;
 constexpr int kThreads = 512;
 constexpr int kPh = kThreads / kTs;  // column phases of a tile
-constexpr int kGroupF = 3;  // float factor blocks per group of the bulk updates (16 KB each)
+constexpr int kGroupF = 4;  // float factor blocks per group of the bulk updates (16 KB each)
 constexpr int kGroupD = 1;  // double factor blocks per group (32 KB each)
 template <class T>
 __host__ __device__ constexpr int group_blocks() { return sizeof(T) == 4 ? kGroupF : kGroupD; }
@@ -100,8 +100,8 @@ __device__ __forceinline__ bool get_tagged(const u64* p, unsigned gen, int* err,
 // the previous tile, so only arithmetic and two block syncs remain on the
 // serial path; the other tiles are updated kGroup at a time (all of their
 // loads issued before any use, for memory-level parallelism). The bulk
-// updates read their factor blocks from shared memory: a group of blocks is
-// copied in (cp.async, 16 bytes per copy) while the previous group is used,
+// updates read their factor blocks from shared memory: a group of four blocks
+// is copied in (cp.async, 16 bytes per copy) while the previous group is used,
 // and the first group of a step's updates is requested before the wait for
 // that step's solution, since the factors do not depend on it. The CTA that
 // will gate the next step (it owns tile t + 2) updates only that tile with
@@ -121,7 +121,8 @@ k_lu_solve_flags(const T* __restrict__ A, int64_t m, const int* __restrict__ per
   T* sbuf = reinterpret_cast<T*>(smem_raw);  // [2][kGa][kTs columns][kTs rows]: factor blocks
   T* acc = sbuf + 2 * kGa * kTs * kTs;       // [my tiles][kTs]
   __shared__ T szb[2][kTs];  // x_t (or y_t) in slot t & 1: the current column and a deferred one
-  __shared__ T red[kGa][kPh][kTs];
+  __shared__ T red[1][kPh][kTs];         // partial sums of the gate's products
+  __shared__ T redb[2][kGa][kPh][kTs];   // partial sums of the bulk updates, by group parity
   __shared__ int s_fail;
   const int64_t nt = (m + kTs - 1) / kTs;
   const int G = gridDim.x, me = blockIdx.x;
@@ -249,23 +250,28 @@ k_lu_solve_flags(const T* __restrict__ A, int64_t m, const int* __restrict__ per
       __syncthreads();
       const int n = (int)imin64(kGa, count - (int64_t)gi * kGa);
       const T* bufp = sbuf + (size_t)(gi & 1) * kGa * kTs * kTs;
+      T(*rd)[kPh][kTs] = redb[gi & 1];
 #pragma unroll
       for (int q = 0; q < kGa; ++q)
         if (q < n) {
           T s = 0;
 #pragma unroll
           for (int j = 0; j < kPer; ++j) s += bufp[((size_t)q * kTs + ph + kPh * j) * kTs + rr] * z[ph + kPh * j];
-          red[q][ph][rr] = s;
+          rd[q][ph][rr] = s;
         }
+      // after this barrier every thread is done with the buffer of group gi
+      // (the next group's copies may overwrite it) and the partial sums are
+      // complete; the sums of group gi + 1 go to the other half of redb, so
+      // no barrier is needed after the accumulation below
       __syncthreads();
       if (ph < n) {
         T sum = 0;
 #pragma unroll
-        for (int q = 0; q < kPh; ++q) sum += red[ph][q][rr];
+        for (int q = 0; q < kPh; ++q) sum += rd[ph][q][rr];
         acc[((u0 + ((int64_t)gi * kGa + ph) * step) / G) * kTs + rr] -= sum;
       }
-      __syncthreads();  // the buffer of group gi is free for group gi + 2
     }
+    __syncthreads();  // the accumulators are complete before anything reads them
   };
   // sz = the solution of tile t: this CTA's own copy, or the published one
   // (waiting for its words to carry this launch's generation; `all`: every
