@@ -206,12 +206,15 @@ int stokes_precond_apply_prec(stokes_geom* g, const double* v, double* z, int pr
  *             Arnoldi, Givens and the least-squares update always FP64; the
  *             true residual, recomputed at every restart, is that of the
  *             chosen operator (FP32 stalls near single precision), except
- *             that DF64 solves take it with the native FP64 operator; a
- *             DF64 restart cycle that starts within 1e4 tol of the
- *             tolerance runs its Arnoldi steps on the FP32 operator: it
- *             only has to reduce the residual by at most 1e4, within the
- *             FP32 operator's accuracy on a correction, and the next FP64
- *             residual decides convergence) or
+ *             in DF64 solves: a restart starts from the double-float
+ *             residual, and convergence is decided only by the native FP64
+ *             operator, which recomputes the residual when the double-float
+ *             one reaches tol or stops falling (a cycle started from a
+ *             double-float residual aims at 0.3 tol); a DF64 cycle that
+ *             starts within 1e4 tol of the tolerance runs its Arnoldi steps
+ *             on the FP32 operator: it only has to reduce the residual by at
+ *             most 1e4, within the FP32 operator's accuracy on a
+ *             correction; true_relres_out is always an FP64 residual) or
  *             STOKES_MIXED_IR
  *             (iterative refinement: outer residual with the FP64 operator,
  *             corrections by GMRES on the FP32 operator until its Arnoldi
