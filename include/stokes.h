@@ -214,7 +214,8 @@ int stokes_precond_apply_prec(stokes_geom* g, const double* v, double* z, int pr
  *             starts within 1e4 tol of the tolerance runs its Arnoldi steps
  *             on the FP32 operator: it only has to reduce the residual by at
  *             most 1e4, within the FP32 operator's accuracy on a
- *             correction; true_relres_out is always an FP64 residual) or
+ *             correction; when the solve converges or reaches max_iter,
+ *             true_relres_out is an FP64 residual) or
  *             STOKES_MIXED_IR
  *             (iterative refinement: outer residual with the FP64 operator,
  *             corrections by GMRES on the FP32 operator until its Arnoldi
