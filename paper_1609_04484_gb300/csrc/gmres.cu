@@ -382,11 +382,16 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
   // tolerance or stopped falling (from then on every restart uses FP64).
   // A cycle that starts from a double-float residual aims kDfResMargin
   // below the tolerance, to cover that residual's error.
+  // A refinement cycle (started from a double-float residual) that reports
+  // convergence goes straight to the FP64 residual: its double-float one
+  // would only confirm what the FP64 one decides.
   bool df_res = precision == STOKES_DF64 && !inner && !left;
   double df_prev = -1.0;
   bool from_df = false;
+  bool refined_converged = false;  // the last cycle started from a double-float residual and converged
   while (true) {
     // true residual r = f - A x
+    if (refined_converged) df_res = false;
     const int rprec = (precision == STOKES_DF64 && !inner) ? (df_res ? STOKES_DF64 : STOKES_FP64) : precision;
     double rn = residual(rprec);
     from_df = false;
@@ -505,6 +510,7 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
                    "operator %s\n",
                    hstate[1], hstate[0], hstate[2], res.relres, from_df ? "df64 residual" : "true residual",
                    op_prec == STOKES_FP32 ? "fp32" : (op_prec == STOKES_DF64 ? "df64" : "fp64"));
+    refined_converged = from_df && hstate[0] && !hstate[2];
     if (inner && hstate[0] && !hstate[2]) {
       res.iters = iters;
       res.relres = res.pc_relres = -1.0;  // not evaluated

@@ -331,10 +331,11 @@ def test_profile_records_pair_launches(S, dev):
         cycles = -(-iters // 30)
         # one pair launch per iteration (double-float, or FP32 in a cycle that
         # starts within 1e4 tol of the tolerance); one double-float launch for
-        # the residual each restart starts from; the FP64 kernel only confirms
-        # convergence (at least once, at most once per restart); flexible
-        # GMRES applies the preconditioner once per iteration
-        assert iters + cycles <= n + n32 <= iters + cycles + 2
+        # the residual each restart starts from, except after a refinement
+        # cycle that converged (straight to FP64); the FP64 kernel only
+        # confirms convergence (at least once, at most once per restart);
+        # flexible GMRES applies the preconditioner once per iteration
+        assert iters + cycles - 1 <= n + n32 <= iters + cycles + 2
         assert 1 <= n64 <= cycles
         assert units == pytest.approx(n * g.n_nodes**2)
         assert ms > 0
