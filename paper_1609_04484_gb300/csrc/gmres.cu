@@ -374,9 +374,10 @@ static SolveResult gmres_core(Geom& g, const double* f, double* x, double tol, i
     return rn;
   };
   // Double-float solves (right preconditioner): the residual a restart
-  // starts from is taken with the double-float operator, whose error
-  // (~1e-12 of the sum of the terms' magnitudes, amplified by large
-  // densities) is small against a residual well above the tolerance;
+  // starts from is taken with the double-float operator, whose error (a
+  // small multiple of 2^-44 times the sum of the terms' magnitudes,
+  // amplified by large densities) is small against a residual well above
+  // the tolerance;
   // convergence is decided by the native FP64 operator only, which
   // recomputes the residual whenever the double-float one is at the
   // tolerance or stopped falling (from then on every restart uses FP64).
