@@ -175,10 +175,14 @@ int stokes_precond_setup_twogrid(stokes_geom* g, int coarsen);
  *   STOKES_TG_COARSE_LU       the float LU factors through persistent
  *                             triangular solves (the same 4 m^2 bytes per
  *                             apply, no inversion)
- * stokes_precond_setup_twogrid(g, q) is the AUTO mode. The coarse LU's
- * panels are factored by one cooperative launch each for 8192 or more
- * coarse unknowns, by three launches per column below; the environment
- * variable STOKES_TG_PANEL=coop or =launches forces either (same result). */
+ * stokes_precond_setup_twogrid(g, q) is the AUTO mode. The coarse LU is
+ * blocked and right-looking: from 8192 coarse unknowns on it takes
+ * 128-column panels, each factored as two 64-column sub-panels by one
+ * cooperative launch apiece (three launches per column below that size),
+ * and its trailing updates run on the tensor cores (three TF32 products per
+ * term; STOKES_TG_GEMM=simt keeps the CUDA-core GEMM). The environment
+ * variable STOKES_TG_PANEL=coop or =launches forces either panel path (same
+ * factors bit for bit). */
 enum stokes_tg_coarse { STOKES_TG_COARSE_AUTO = 0, STOKES_TG_COARSE_INVERSE = 1, STOKES_TG_COARSE_LU = 2 };
 int stokes_precond_setup_twogrid_ex(stokes_geom* g, int coarsen, int coarse_mode);
 
